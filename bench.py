@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Throughput of the randomized-DOT hot path: sampled misfit + gradient evaluations/s.
+
+One step = one whole evaluation at a new PaLS parameter vector p: PaLS -> mu,
+operator coefficients, right-hand sides [B W | C V], the block Krylov solve of
+the l_s forward and l_d adjoint columns, restriction S = (CV)^T U, residual,
+misfit, sensitivity g_mu and the PaLS chain rule g_p.
+
+Default workload: 128 x 128 x 64 cells (1,048,576), omega = 2 pi 100 MHz (complex
+symmetric A, COCG), 256 sources x 256 detectors sampled as 32 + 32 simultaneous
+columns, 125 RBFs, complex64 Krylov inside FP64 refinement to relative residual
+1e-10.  Inputs are synthetic (seeded), shaped like the paper's 3D workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1706_05586_gb300 import synth  # noqa: E402
+
+METRIC = "misfit+gradient evals/s at 1M voxels"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="dot128x128x64_w100MHz", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        idx = local_rank
+        if vis:
+            parts = [x.strip() for x in vis.split(",") if x.strip()]
+            if local_rank < len(parts) and parts[local_rank].isdigit():
+                idx = int(parts[local_rank])
+        self.idx = idx
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(kernel_key, workload):
+    """dram bytes per launch of a kernel from a committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for ln in open(path):
+        if ln.startswith("#") or not ln.strip():
+            continue
+        parts = ln.split()
+        if len(parts) >= 4 and parts[0] == kernel_key and parts[1] == workload:
+            return parts
+    return None
+
+
+# ---------------------------------------------------------------- our arm
+def setup_problem(D, ctx, wl, inp, prec, rtol, log):
+    """Synthesize D and the data M with the library itself, then set the sampling."""
+    D.dot_set_grid(ctx, wl.nx, wl.ny, wl.nz, wl.h, wl.bc)
+    D.dot_set_omega(ctx, wl.omega_nu)
+    D.dot_set_diffusion(ctx, np.full(wl.n, 1.0 / 30.0))
+    D.dot_set_pals(ctx, inp.p_true, synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
+    mu_true = D.dot_get_mua(ctx, wl.n)
+    Dfield = synth.diffusion_from_mua(mu_true)
+    D.dot_set_diffusion(ctx, Dfield)
+    D.dot_set_sources(ctx, inp.B)
+    D.dot_set_detectors(ctx, inp.C)
+    t0 = time.perf_counter()
+    D.dot_set_sampling(ctx, np.eye(wl.ns), np.eye(wl.nd))
+    D.dot_set_solver(ctx, D.PREC_MIXED, 1e-10, 0)
+    Mclean, _ = D.dot_measurements(ctx, wl.ns, wl.nd, wl.omega_nu != 0.0)
+    log(f"data synthesis ({wl.ns}+{wl.nd} columns): {time.perf_counter() - t0:.1f} s")
+    M = synth.add_noise(Mclean, inp)
+    D.dot_set_data(ctx, M)
+    D.dot_set_sampling(ctx, inp.W, inp.V)
+    D.dot_set_solver(ctx, D.PREC_MIXED if prec == "mixed" else D.PREC_FP64, rtol, 0)
+    return Dfield, M
+
+
+def p_sequence(inp, count, seed=7):
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal(inp.p0.size)
+    d[1::5] = 0.0  # keep the dilations fixed
+    return [inp.p0 + 1e-3 * (k + 1) * d for k in range(count)]
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1706_05586_gb300 import dot as D
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    log = (lambda m: print(f"[bench] {m}", file=sys.stderr, flush=True)) if rank == 0 else (lambda m: None)
+    wl = synth.WORKLOADS[args.workload]
+    inp = synth.draw(wl)
+    stream = torch.cuda.Stream()          # the library's kernels and the timing events share it
+    torch.cuda.set_stream(stream)
+    ctx = D.dot_create(local)
+    D.dot_set_stream(ctx, stream.cuda_stream)
+    Dfield, M = setup_problem(D, ctx, wl, inp, args.precision, args.rtol, log)
+    ps = p_sequence(inp, args.warmup + args.steps)
+    p_dev = torch.tensor(np.stack(ps), dtype=torch.float64, device=f"cuda:{local}")
+    pals = (synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
+    m0 = wl.m0
+
+    def step(k):
+        D.dot_set_pals_dev(ctx, m0, p_dev[k].data_ptr(), *pals)
+        return D.dot_gradient(ctx, wl.np_)
+
+    for k in range(args.warmup):
+        f, g, _ = step(k)
+        st = D.dot_get_stats(ctx)
+        log(f"warmup {k}: f={f:.6e} iters={st['iters_max']} outer={st['outer_steps']} "
+            f"relres={st['relres_max']:.2e} solve={st['ms_solve']:.1f} ms")
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    launches0 = D.dot_get_stats(ctx)["kernel_launches"]
+    iters = []
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    D.dot_set_kernel_timing(ctx, 1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(args.warmup, args.warmup + args.steps):
+        f, g, _ = step(k)
+        st = D.dot_get_stats(ctx)
+        iters.append((st["iters_max"], st["outer_steps"], st["relres_max"]))
+    ev1.record(stream)
+    barrier()
+    D.dot_set_kernel_timing(ctx, 0)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    kt = D.dot_get_kernel_timing(ctx)
+    launches = D.dot_get_stats(ctx)["kernel_launches"] - launches0
+    ms_max = ms
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = args.steps * ws / (ms_max / 1e3)
+    f_last, g_last = f, g
+
+    # dominant Krylov kernel against the HBM roofline
+    peaks, peak_kind = measured_peaks()
+    dom = max(kt, key=lambda nm: kt[nm]["ms"])
+    kd = kt[dom]
+    achieved = kd["bytes"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else 0.0
+    per_launch_bytes = kd["bytes"] / max(kd["launches"], 1)
+    trow = ncu_traffic(dom, args.workload)
+    traffic = None
+    if trow is not None:
+        try:
+            traffic = float(trow[3])
+        except ValueError:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": kd["ms"] / max(kd["launches"], 1),
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "kernels": {nm: {"launches": kt[nm]["launches"], "ms": round(kt[nm]["ms"], 3),
+                                 "GBps": round(kt[nm]["bytes"] / (kt[nm]["ms"] * 1e-3) / 1e9, 1) if kt[nm]["ms"] else 0}
+                            for nm in kt}}
+
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "c64+f64" if args.precision == "mixed" and wl.omega_nu else
+                    ("f32+f64" if args.precision == "mixed" else ("c128" if wl.omega_nu else "f64")),
+           "data": "synthetic (seeded PaLS phantom, Gaussian sources/detectors, data from the FP64-refined "
+                   "forward model + 1% noise)",
+           "config": {"workload": args.workload, "grid": [wl.nx, wl.ny, wl.nz], "n_voxels": wl.n, "h_cm": wl.h,
+                      "omega_over_nu": wl.omega_nu, "ns": wl.ns, "nd": wl.nd, "ls": wl.ls, "ld": wl.ld,
+                      "m0": wl.m0, "n_params": wl.np_, "precision": args.precision, "rtol": args.rtol,
+                      "krylov_iters_per_step": [it[0] for it in iters], "outer_steps": [it[1] for it in iters],
+                      "relres_max": max(it[2] for it in iters),
+                      "l2": "inputs larger than L2 (each Krylov block vector >= 512 MiB)",
+                      "parallelism": f"replicas x{ws}"},
+           "clocks": clk, "gpu_launches": int(launches), "roofline": roofline}
+
+    # plain FP64 GPU path at the last p: accuracy of the mixed path and its own throughput
+    if not args.no_fp64_compare and args.precision == "mixed":
+        D.dot_set_solver(ctx, D.PREC_FP64, args.rtol, 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f64, g64, _ = D.dot_gradient(ctx, wl.np_)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        out["fp64_path"] = {"evals_per_s": round(1e3 / ms64, 4), "ms_per_eval": round(ms64, 1),
+                            "iters": D.dot_get_stats(ctx)["iters_max"]}
+        out["err_vs_fp64"] = {"f": abs(f_last - f64) / abs(f64),
+                              "g": float(np.linalg.norm(g_last - g64) / np.linalg.norm(g64))}
+        D.dot_set_solver(ctx, D.PREC_MIXED, args.rtol, 0)
+
+    # end to end through the C ABI with host buffers (all inputs copied every step)
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hD = pin(Dfield)
+        hB = tuple(pin(a) for a in inp.B)
+        hC = tuple(pin(a) for a in inp.C)
+        hW = pin(np.asfortranarray(inp.W).ravel(order="F"))
+        hV = pin(np.asfortranarray(inp.V).ravel(order="F"))
+        hp = [pin(p) for p in ps]
+        nnzB, nnzC = hB[2].size, hC[2].size
+        h2d = (wl.n * 8 + wl.np_ * 8 + (wl.n + 1) * 8 + nnzB * 12 + 2 * (wl.n + 1) * 8 + nnzC * 24
+               + (wl.nd + 1) * 8 + M.size * 16 + hW.size * 8 + hV.size * 8)
+        d2h = 8 + wl.np_ * 8
+        Mc = np.asfortranarray(M)
+        Wf = hW.reshape(wl.ns, wl.ls, order="F")
+        Vf = hV.reshape(wl.nd, wl.ld, order="F")
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        t0 = time.perf_counter()
+        for k in range(args.warmup, args.warmup + args.steps):
+            D.dot_set_diffusion(ctx, hD)
+            D.dot_set_pals(ctx, hp[k], *pals)
+            D.dot_set_sources(ctx, hB)
+            D.dot_set_detectors(ctx, hC)
+            D.dot_set_data(ctx, Mc)
+            D.dot_set_sampling(ctx, Wf, Vf)
+            D.dot_gradient(ctx, wl.np_)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([te], dtype=torch.float64, device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        out["e2e"] = {"value": round(args.steps * ws / te, 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h)}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, inp, log)
+    D.dot_destroy(ctx)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------- oracle timing
+def oracle_sample(wl, inp, rtol, maxit=None):
+    """Time the oracle's pieces of one evaluation: PaLS, assembly, one column solve."""
+    from oracle import dot_oracle as orc
+    t0 = time.perf_counter()
+    X = orc.cell_centres(wl.nx, wl.ny, wl.nz, wl.h)
+    mu_true = orc.pals_mu(inp.p_true, X, synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
+    Dfield = synth.diffusion_from_mua(mu_true)
+    t1 = time.perf_counter()
+    mu = orc.pals_mu(inp.p0, X, synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
+    A = orc.assemble(Dfield, mu, wl.nx, wl.ny, wl.nz, wl.h, wl.bc, wl.omega_nu)
+    t2 = time.perf_counter()
+    b = orc.dense_of_csc(wl.n, (inp.B[0][:2], inp.B[1][:inp.B[0][1]], inp.B[2][:inp.B[0][1]]))[:, 0]
+    t3 = time.perf_counter()
+    try:
+        _, its = orc.krylov_solve(A, b, rtol=rtol, maxit=maxit)
+        converged = True
+    except RuntimeError:
+        its, converged = maxit, False
+    t4 = time.perf_counter()
+    return {"t_pals_assembly": (t1 - t0) / 2 + (t2 - t1), "t_solve": t4 - t3, "iters": its, "converged": converged}
+
+
+def cpu_baseline(wl, inp, log):
+    s = oracle_sample(wl, inp, 1e-10)
+    per_eval = s["t_pals_assembly"] + (wl.ns + wl.nd) * s["t_solve"]
+    log(f"oracle sample: {s}")
+    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (numpy/scipy, single-threaded) on the same workload: PaLS + assembly "
+                       f"({s['t_pals_assembly']:.2f} s) and one physical-source COCG solve to rtol 1e-10 "
+                       f"({s['iters']} iterations, {s['t_solve']:.2f} s); its evaluation solves every physical "
+                       f"source and detector, so one evaluation = PaLS + assembly + {wl.ns + wl.nd} such solves "
+                       f"= {per_eval:.0f} s"),
+            "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl = synth.WORKLOADS[args.workload]
+    inp = synth.draw(wl)
+    cap = 60
+    for _ in range(args.warmup):
+        oracle_sample(wl, inp, 1e-10, maxit=5)
+    t0 = time.perf_counter()
+    samples = [oracle_sample(wl, inp, 1e-10, maxit=cap) for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    # per-iteration cost of a column solve, scaled to a full evaluation with the iteration
+    # count of one converged column solve measured once below the timed steps
+    t_it = statistics.mean(s["t_solve"] / max(s["iters"], 1) for s in samples)
+    t_pa = statistics.mean(s["t_pals_assembly"] for s in samples)
+    conv = oracle_sample(wl, inp, 1e-10, maxit=None) if args.steps else None
+    its = conv["iters"] if conv else cap
+    per_eval = t_pa + (wl.ns + wl.nd) * its * t_it
+    value = 1.0 / per_eval
+    sample = (f"oracle per step: PaLS + assembly + {cap} COCG iterations of one physical-source column "
+              f"({statistics.mean(s['t_solve'] for s in samples):.2f} s); scaled by {wl.ns + wl.nd} columns x "
+              f"{its} iterations (one converged column solve) to one evaluation = {per_eval:.0f} s")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128" if wl.omega_nu else "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "grid": [wl.nx, wl.ny, wl.nz], "n_voxels": wl.n,
+                      "ns": wl.ns, "nd": wl.nd, "ls": wl.ls, "ld": wl.ld, "m0": wl.m0},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * dot.h - C ABI of the GB300 hot path for randomized diffuse optical tomography
+ * (DOT) with simultaneous random and optimized sources and detectors
+ * (Aslan, de Sturler, Kilmer).
+ *
+ * The library evaluates, for a fixed sampling (W, V), the quantities of Sec. 3:
+ *   - forward block solves  A(mu) U = B W    (Eq. (EsTResidual), z_i in the paper)
+ *   - adjoint block solves  A^T Z = C V      (Sec. 3.3, y_j in the paper)
+ *   - sampled misfit f = ||V^T (C^T A^{-1} B - M) W||_F^2     (Theorem 1)
+ *   - sampled mu-Jacobian rows -Z_l (.) U_i  (Eq. (Jacobiancomp) and
+ *     Eq. (Jacobian kth column): dA/dmu_v = e_v e_v^T when D is known)
+ *   - PaLS chain rule to the shape parameters p   (Sec. 2, Eq. (absorption const))
+ *   - misfit gradient 2 Re J^T conj(r_s)          (Eq. (UnbiasedGrad))
+ * where A(mu) + i(omega/nu) I is the cell-centred finite-volume form of the
+ * diffusion equation of Sec. 2, Eq. (PDE), with Robin or Dirichlet faces.
+ *
+ * Conventions
+ *   - Every call returns an int status: DOT_OK (0) or a negative DOT_E* code.
+ *     dot_last_error() returns a message for the calling thread's last error.
+ *   - Plain entry points take HOST pointers; the library copies what it needs
+ *     into device memory it owns (setters copy, the caller keeps ownership).
+ *     Entry points ending in _dev take DEVICE pointers valid on the context's
+ *     device; they are read or written in order on the context's stream.
+ *   - Dense matrices are column-major.  Complex values (omega != 0) are
+ *     interleaved (re, im) pairs of doubles.
+ *   - Voxel index v = i + nx (j + ny k) of the cell centred at
+ *     ((i+1/2)h, (j+1/2)h, (k+1/2)h); k = 0 is the top face (x3 = 0).
+ *   - Face order for boundary flags: -x, +x, -y, +y, -z (top), +z (bottom).
+ *   - PaLS parameters: 5 per RBF, (alpha_j, beta_j, chi_xj, chi_yj, chi_zj).
+ *   - Sampled Jacobian rows are ordered r = l + l_d * i (vec of V^T R W).
+ *   - Results are cached: an evaluation call reuses the block solve while no
+ *     setter has changed its inputs.  Every setter invalidates what depends on it.
+ *   - A context is not thread-safe; use one context per thread.
+ */
+#ifndef DOT_H
+#define DOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DOT_OK          0
+#define DOT_EINVAL     -1  /* bad argument (size, pointer, flag)                 */
+#define DOT_ESTATE     -2  /* a required setter has not been called              */
+#define DOT_ENOMEM     -3  /* device allocation failed                           */
+#define DOT_ECUDA      -4  /* CUDA runtime error                                 */
+#define DOT_ENOTCONV   -5  /* Krylov solve hit maxit; outputs are still written  */
+#define DOT_EBREAKDOWN -6  /* CG/COCG breakdown (zero p^T A p or rho)            */
+
+/* boundary flags */
+#define DOT_BC_ROBIN      0  /* 0.25 eta + (D/2) d eta / d xi = 0, Eq. (PDE)      */
+#define DOT_BC_DIRICHLET  1  /* eta = 0, Eq. (PDE) lateral faces                  */
+
+/* solver precision */
+#define DOT_PREC_FP64   0  /* FP64 / complex128 Jacobi CG (omega = 0) or COCG     */
+#define DOT_PREC_MIXED  1  /* FP32 / complex64 CG or COCG inside FP64 iterative
+                              refinement; residuals, updates and all outputs FP64 */
+
+typedef struct dot_ctx dot_ctx;
+
+typedef struct dot_stats {
+    int32_t k;               /* columns of the last block solve (l_s + l_d)            */
+    int32_t iters_max;       /* max over columns of Krylov iterations (summed over
+                                refinement steps in mixed precision)                   */
+    int64_t iters_sum;       /* sum over columns of Krylov iterations                 */
+    int32_t outer_steps;     /* FP64 refinement steps of the last solve (0 for FP64)  */
+    int32_t status;          /* status of the last block solve                        */
+    double  relres_max;      /* max over columns of ||b - A x|| / ||b|| (FP64 true
+                                residual in mixed precision, recurrence residual in
+                                FP64 mode)                                             */
+    int64_t columns_solved;  /* cumulative number of PDE solves (columns)             */
+    int64_t block_solves;    /* cumulative number of block solves                     */
+    double  ms_setup;        /* last: PaLS + coefficients + right-hand sides          */
+    double  ms_solve;        /* last: block Krylov solve                              */
+    double  ms_post;         /* last: restriction, misfit, sensitivity, chain rule    */
+    int64_t kernel_launches; /* cumulative number of this library's kernel launches   */
+} dot_stats;
+
+/* Per-kernel device time of the Krylov kernels, accumulated while timing is on.
+ * Index 0: stencil q = A p with p^T q; 1: x/r update with r^T M^{-1} r and ||r||^2;
+ * 2: direction update p = M^{-1} r + beta p; 3: FP64 refinement residual b - A x.
+ * bytes: algorithmic DRAM bytes of those launches (each vector element of an
+ * active column read or written once, coefficients once per launch). */
+typedef struct dot_kernel_timing {
+    int64_t launches[4];
+    double  ms[4];
+    double  bytes[4];
+} dot_kernel_timing;
+
+/* Context: binds a CUDA device and owns every device buffer.
+ * dot_create: *out receives the handle; device is a CUDA ordinal.  Creates a
+ * private non-blocking stream.  Errors: DOT_EINVAL, DOT_ECUDA. */
+int dot_create(dot_ctx** out, int device);
+/* Frees every device buffer and the private stream.  NULL is accepted. */
+int dot_destroy(dot_ctx* ctx);
+/* Message for the calling thread's last failed call ("" if none).  The pointer
+ * stays valid until the thread's next failed call. */
+const char* dot_last_error(void);
+/* Make subsequent work run on `stream` (a cudaStream_t of the context's device,
+ * e.g. torch.cuda.current_stream().cuda_stream); NULL restores the private stream. */
+int dot_set_stream(dot_ctx* ctx, void* stream);
+
+/* Grid (Sec. 2, Eq. (PDE) and Eq. (Eq:compmeas)): nx*ny*nz cells of size h (cm),
+ * bc[6] boundary flags.  Invalidates everything sized by the grid. */
+int dot_set_grid(dot_ctx* ctx, int nx, int ny, int nz, double h, const int bc[6]);
+/* omega / nu (cm^-1) of the frequency term i(omega/nu) E, E = I on the
+ * cell-centred grid.  0 selects real arithmetic (CG), != 0 complex (COCG). */
+int dot_set_omega(dot_ctx* ctx, double omega_over_nu);
+/* Diffusion coefficient D (N doubles, cm), known and held fixed (Sec. 2). */
+int dot_set_diffusion(dot_ctx* ctx, const double* D);
+/* Absorption mu_a (N doubles, cm^-1) set directly; gradients are then taken
+ * with respect to mu (N entries).  Replaces any PaLS parameters. */
+int dot_set_mua(dot_ctx* ctx, const double* mu);
+/* PaLS absorption (Sec. 2): phi(x) = sum_j alpha_j psi(||beta_j (x - chi_j)||^dagger),
+ * psi = Wendland psi_{2,1}, ||y||^dagger = sqrt(||y||^2 + gamma^2),
+ * mu = mu_in H_eps(phi - c) + mu_out (1 - H_eps(phi - c)) with the C^1 sine ramp
+ * H_eps of half width eps.  p: 5*m0 doubles.  Gradients are then with respect to p. */
+int dot_set_pals(dot_ctx* ctx, int m0, const double* p, double mu_in, double mu_out,
+                 double c, double eps, double gamma);
+/* As dot_set_pals with p a device pointer (5*m0 doubles) read on the context stream. */
+int dot_set_pals_dev(dot_ctx* ctx, int m0, const double* p_dev, double mu_in, double mu_out,
+                     double c, double eps, double gamma);
+
+/* Physical sources B (N x ns) and detectors C (N x nd) as CSC: colptr[ncol+1]
+ * (int64), rows[nnz] (int32 voxel indices, each column's rows distinct),
+ * vals[nnz] (double).  Eq. (Eq:compmeas): b_i are the source terms, rows of C^T the
+ * detectors. */
+int dot_set_sources(dot_ctx* ctx, int ns, const int64_t* colptr, const int32_t* rows,
+                    const double* vals);
+int dot_set_detectors(dot_ctx* ctx, int nd, const int64_t* colptr, const int32_t* rows,
+                      const double* vals);
+/* Data M (nd x ns, column-major; the paper's D of Eq. (MartixR)).  is_complex = 1:
+ * interleaved complex (required when omega != 0), 0: real. */
+int dot_set_data(dot_ctx* ctx, const double* M, int is_complex);
+/* Sampling matrices W (ns x ls) and V (nd x ld), column-major, already scaled
+ * (Eqs. (defW), (defV): l^{-1/2} times i.i.d. zero-mean unit-variance entries,
+ * or optimized / complemented columns, Eqs. (newW), (newV)). */
+int dot_set_sampling(dot_ctx* ctx, int ls, const double* W, int ld, const double* V);
+/* Krylov settings: precision DOT_PREC_*, relative residual target rtol
+ * (||b - A x||_2 <= rtol ||b||_2 per column), maxit Krylov iterations per column
+ * (per refinement step in mixed precision; 0 selects 10 (nx + ny + nz)).
+ * ls + ld (the block width) may not exceed 1024. */
+int dot_set_solver(dot_ctx* ctx, int precision, double rtol, int maxit);
+/* Mixed precision only: inner relative tolerance of each FP32 solve (default 1e-5)
+ * and the maximum number of FP64 refinement steps (default 8). */
+int dot_set_refinement(dot_ctx* ctx, double inner_rtol, int max_outer);
+
+/* Sampled misfit f = ||V^T (C^T A^{-1} B - M) W||_F^2 (Theorem 1 / Eq. (EsTResidual);
+ * no factor 1/2; complex: sum of squared real and imaginary parts).  Solves the
+ * l_s + l_d columns [BW | CV] as one block.  Returns DOT_ENOTCONV or
+ * DOT_EBREAKDOWN (with f still written) when a column failed. */
+int dot_misfit(dot_ctx* ctx, double* f);
+/* Sampled computed measurements S = V^T C^T A^{-1} B W (ld x ls, column-major,
+ * complex interleaved when omega != 0); with W = I, V = I this is the full
+ * C^T A^{-1} B of Eq. (Eq:compmeas).  Does not need data. */
+int dot_measurements(dot_ctx* ctx, double* S);
+/* f and its gradient: g (5*m0 doubles) with respect to p after dot_set_pals,
+ * or (N doubles) with respect to mu after dot_set_mua.  g = 2 Re J^T conj(vec R_s)
+ * with J the sampled Jacobian of Eq. (Jacobian kth column). */
+int dot_gradient(dot_ctx* ctx, double* f, double* g);
+/* Sampled mu-Jacobian J_mu[(l + ld i), v] = -Z_l[v] U_i[v]  ((ls*ld) x N,
+ * column-major; complex interleaved when omega != 0).  (ls*ld*N) values. */
+int dot_jacobian_mua(dot_ctx* ctx, double* J);
+/* Sampled p-Jacobian J_p = J_mu dmu/dp  ((ls*ld) x 5*m0, column-major; complex
+ * interleaved when omega != 0).  Needs dot_set_pals. */
+int dot_jacobian_p(dot_ctx* ctx, double* Jp);
+
+/* Inspection.  dot_get_mua: the absorption field in use (N doubles).
+ * dot_get_fields: forward fields U (N x ls) and adjoint fields Z (N x ld),
+ * column-major (complex interleaved when omega != 0); either pointer may be NULL.
+ * dot_get_stats: counters of the last evaluation. */
+int dot_get_mua(dot_ctx* ctx, double* mu);
+int dot_get_fields(dot_ctx* ctx, double* U, double* Z);
+int dot_get_stats(dot_ctx* ctx, dot_stats* stats);
+/* Kernel timing: enable != 0 resets the counters and records CUDA events around
+ * every Krylov kernel launch (on the context stream); 0 stops recording. */
+int dot_set_kernel_timing(dot_ctx* ctx, int enable);
+int dot_get_kernel_timing(dot_ctx* ctx, dot_kernel_timing* out);
+
+/* One operator application y = (A(mu) + i(omega/nu) I) x on k columns
+ * (N x k, column-major, complex interleaved when omega != 0) in FP64.
+ * The 7-point stencil of the block solve, exposed for testing. */
+int dot_apply(dot_ctx* ctx, int k, const double* x, double* y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOT_H */

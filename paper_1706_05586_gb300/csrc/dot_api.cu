@@ -1,0 +1,914 @@
+// C-ABI runtime of the DOT hot path: context, setters, evaluation pipeline.
+//
+// Pipeline of one evaluation (each step a kernel of this library):
+//   PaLS -> mu (fields.cu) -> operator coefficients -> right-hand sides [BW | CV]
+//   -> block Krylov solve (krylov.cu) -> restriction S = (CV)^T U, R_s, f
+//   -> sensitivity g_mu -> PaLS chain rule g_p.
+// Results are cached per stage and invalidated by the setters they depend on.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dot.h"
+#include "dot_internal.h"
+
+using namespace dotk;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(expr)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(DOT_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+#define TRY(expr)                  \
+    do {                           \
+        int rc_ = (expr);          \
+        if (rc_ != DOT_OK) return rc_; \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+int ensure(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.p && b.bytes >= bytes) return DOT_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return fail(DOT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return DOT_OK;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+}  // namespace
+
+struct dot_ctx {
+    int device = 0;
+    int num_sms = 152;
+    cudaStream_t own = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int* h_flag = nullptr;  // pinned host word for polling n_active
+
+    bool grid_set = false;
+    int nx = 0, ny = 0, nz = 0;
+    double h = 0;
+    int bc[6] = {0, 0, 0, 0, 0, 0};
+    int64_t n = 0;
+    double w = 0.0;
+
+    bool D_set = false;
+    DevBuf D;
+    int mu_mode = 0;  // 0 unset, 1 direct, 2 PaLS
+    DevBuf mu, phi, wdmu;
+    int m0 = 0;
+    DevBuf p;
+    double mu_in = 0, mu_out = 0, cut = 0, eps = 1, gamma = 0;
+
+    bool coef_valid = false;
+    DevBuf cx, cy, cz, dre, dinv64, cx32, cy32, cz32, dre32, dinv32;
+
+    int ns = 0, nd = 0;
+    DevBuf rpB, ciB, vB, rpC, ciC, vC, cpC, rwC, vCc;
+
+    int ls = 0, ld = 0;
+    DevBuf W, V;
+
+    bool M_set = false;
+    DevBuf M, MW, P;
+    bool P_valid = false;
+
+    int prec = DOT_PREC_FP64;
+    double rtol = 1e-10;
+    int maxit = 0;
+    double inner_rtol = 1e-5;
+    int max_outer = 8;
+
+    // block vectors (FP64 and FP32 precisions)
+    DevBuf b64, x64, r64, p64, q64, x32, r32, p32, q32;
+    // per-column state
+    DevBuf cs_rho, cs_alpha, cs_beta, cs_rr, cs_bb, cs_active, cs_iters, cs_status, cs_misc, cs_partA, cs_partB;
+    DevBuf rs_bb, rs_rr, rs_scale, rs_active, rs_misc, rs_partB;
+    bool fields_valid = false;
+    int fields_status = DOT_OK;
+    int kp = 0;
+
+    bool post_valid = false;
+    DevBuf Tm, S, Rs, f, gmu, gp, J, tmp;
+
+    dot_stats stats{};
+
+    // kernel timing (dot_set_kernel_timing)
+    bool timing = false;
+    cudaEvent_t tev[8 * 4 + 2] = {};
+    dot_kernel_timing kt{};
+};
+
+namespace {
+
+bool cplx(const dot_ctx* c) { return c->w != 0.0; }
+size_t esz64(const dot_ctx* c) { return cplx(c) ? 16 : 8; }
+size_t esz32(const dot_ctx* c) { return cplx(c) ? 8 : 4; }
+void count(dot_ctx* c, int launches) { c->stats.kernel_launches += launches; }
+
+void invalidate_coef(dot_ctx* c) {
+    c->coef_valid = false;
+    c->fields_valid = false;
+    c->post_valid = false;
+}
+void invalidate_fields(dot_ctx* c) {
+    c->fields_valid = false;
+    c->post_valid = false;
+}
+
+int need_ctx(dot_ctx* c) {
+    if (!c) return fail(DOT_EINVAL, "null context");
+    CK(cudaSetDevice(c->device));
+    return DOT_OK;
+}
+
+int need_grid(dot_ctx* c) {
+    TRY(need_ctx(c));
+    if (!c->grid_set) return fail(DOT_ESTATE, "dot_set_grid has not been called");
+    return DOT_OK;
+}
+
+int upload(dot_ctx* c, DevBuf& b, const void* host, size_t bytes) {
+    TRY(ensure(b, bytes));
+    CK(cudaMemcpyAsync(b.p, host, bytes, cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return DOT_OK;
+}
+
+int kp_limit_check(dot_ctx* c) {
+    if (c->ls + c->ld > 1024) return fail(DOT_EINVAL, "ls + ld exceeds 1024");
+    return DOT_OK;
+}
+
+OpRaw op64(const dot_ctx* c) {
+    OpRaw o;
+    o.cx = c->cx.p;
+    o.cy = c->cy.p;
+    o.cz = c->cz.p;
+    o.dre = c->dre.p;
+    o.dinv = c->dinv64.p;
+    o.w = c->w;
+    o.nx = c->nx;
+    o.ny = c->ny;
+    o.nz = c->nz;
+    return o;
+}
+OpRaw op32(const dot_ctx* c) {
+    OpRaw o = op64(c);
+    o.cx = c->cx32.p;
+    o.cy = c->cy32.p;
+    o.cz = c->cz32.p;
+    o.dre = c->dre32.p;
+    o.dinv = c->dinv32.p;
+    return o;
+}
+
+// ------------------------------------------------------------------ stages
+int ensure_coefficients(dot_ctx* c) {
+    if (c->coef_valid) return DOT_OK;
+    if (!c->D_set) return fail(DOT_ESTATE, "dot_set_diffusion has not been called");
+    if (c->mu_mode == 0) return fail(DOT_ESTATE, "neither dot_set_mua nor dot_set_pals has been called");
+    const int64_t n = c->n;
+    if (c->mu_mode == 2) {
+        TRY(ensure(c->mu, n * 8));
+        TRY(ensure(c->phi, n * 8));
+        TRY(ensure(c->wdmu, n * 8));
+        CK(pals_eval(c->p.as<double>(), c->m0, c->mu_in, c->mu_out, c->cut, c->eps, c->gamma, c->nx, c->ny, c->nz,
+                     c->h, c->phi.as<double>(), c->mu.as<double>(), c->wdmu.as<double>(), c->s));
+    }
+    for (DevBuf* b : {&c->cx, &c->cy, &c->cz, &c->dre}) TRY(ensure(*b, n * 8));
+    for (DevBuf* b : {&c->cx32, &c->cy32, &c->cz32, &c->dre32}) TRY(ensure(*b, n * 4));
+    TRY(ensure(c->dinv64, n * 16));
+    TRY(ensure(c->dinv32, n * 8));
+    CK(build_coefficients(c->D.as<double>(), c->mu.as<double>(), c->nx, c->ny, c->nz, c->h, c->bc, c->w,
+                          c->cx.as<double>(), c->cy.as<double>(), c->cz.as<double>(), c->dre.as<double>(), c->dinv64.p,
+                          cplx(c), c->cx32.as<float>(), c->cy32.as<float>(), c->cz32.as<float>(),
+                          c->dre32.as<float>(), c->dinv32.p, c->s));
+    count(c, c->mu_mode == 2 ? 2 : 1);
+    c->coef_valid = true;
+    return DOT_OK;
+}
+
+int alloc_colstate(dot_ctx* c, int kp, const Launch& L, ColState* st, RefState* rs) {
+    TRY(ensure(c->cs_rho, kp * 16));
+    TRY(ensure(c->cs_alpha, kp * 16));
+    TRY(ensure(c->cs_beta, kp * 16));
+    TRY(ensure(c->cs_rr, kp * 8));
+    TRY(ensure(c->cs_bb, kp * 8));
+    TRY(ensure(c->cs_active, kp * 4));
+    TRY(ensure(c->cs_iters, kp * 4));
+    TRY(ensure(c->cs_status, kp * 4));
+    TRY(ensure(c->cs_misc, 64));
+    TRY(ensure(c->cs_partA, (size_t)L.grid * kp * 16));
+    TRY(ensure(c->cs_partB, (size_t)L.grid * kp * 8));
+    TRY(ensure(c->rs_bb, kp * 8));
+    TRY(ensure(c->rs_rr, kp * 8));
+    TRY(ensure(c->rs_scale, kp * 8));
+    TRY(ensure(c->rs_active, kp * 4));
+    TRY(ensure(c->rs_misc, 64));
+    TRY(ensure(c->rs_partB, (size_t)L.grid * kp * 8));
+    CK(cudaMemsetAsync(c->cs_misc.p, 0, 64, c->s));
+    CK(cudaMemsetAsync(c->rs_misc.p, 0, 64, c->s));
+    CK(cudaMemsetAsync(c->rs_active.p, 0, kp * 4, c->s));
+    st->rho = c->cs_rho.as<double2>();
+    st->alpha = c->cs_alpha.as<double2>();
+    st->beta = c->cs_beta.as<double2>();
+    st->rr = c->cs_rr.as<double>();
+    st->bb = c->cs_bb.as<double>();
+    st->active = c->cs_active.as<int>();
+    st->iters = c->cs_iters.as<int>();
+    st->status = c->cs_status.as<int>();
+    st->n_active = c->cs_misc.as<int>();
+    st->counter = reinterpret_cast<unsigned*>(c->cs_misc.as<int>() + 4);
+    st->partA = c->cs_partA.as<double2>();
+    st->partB = c->cs_partB.as<double>();
+    rs->bb = c->rs_bb.as<double>();
+    rs->rr = c->rs_rr.as<double>();
+    rs->scale = c->rs_scale.as<double>();
+    rs->active = c->rs_active.as<int>();
+    rs->n_active = c->rs_misc.as<int>();
+    rs->counter = reinterpret_cast<unsigned*>(c->rs_misc.as<int>() + 4);
+    rs->partB = c->rs_partB.as<double>();
+    return DOT_OK;
+}
+
+int read_flag(dot_ctx* c, const int* dev, int* out) {
+    CK(cudaMemcpyAsync(c->h_flag, dev, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    *out = *c->h_flag;
+    return DOT_OK;
+}
+
+constexpr int kPoll = 8;  // iterations between host convergence polls
+
+// Iterate until every column of the block has stopped; returns iterations launched.
+int krylov_loop(dot_ctx* c, ElemKind ek, const OpRaw& o, void* x, void* r, void* p, void* q, int kp,
+                const ColState& st, double rtol, int maxit, const Launch& L, int* launched) {
+    int it = 0, act = 0;
+    TRY(read_flag(c, st.n_active, &act));
+    while (act > 0 && it < maxit + kPoll) {
+        for (int m = 0; m < kPoll; ++m)
+            CK(kry_iteration(ek, o, x, r, p, q, c->n, kp, st, rtol, maxit, L, c->s,
+                             c->timing ? &c->tev[4 * m] : nullptr));
+        count(c, 3 * kPoll);
+        it += kPoll;
+        TRY(read_flag(c, st.n_active, &act));
+        if (c->timing) {
+            for (int m = 0; m < kPoll; ++m)
+                for (int q3 = 0; q3 < 3; ++q3) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, c->tev[4 * m + q3], c->tev[4 * m + q3 + 1]));
+                    c->kt.ms[q3] += ms;
+                    c->kt.launches[q3] += 1;
+                }
+        }
+    }
+    *launched = it;
+    return DOT_OK;
+}
+
+// Algorithmic bytes of the Krylov kernels of one solve: per column-iteration each
+// vector element is read or written once (stencil: p, q; update: x, p, r, q read and
+// x, r written; direction: r, p read, p written), coefficients once per launch.
+void account_bytes(dot_ctx* c, const std::vector<int>& it_h, size_t es, size_t rs, size_t ds) {
+    if (!c->timing) return;
+    double ci = 0.0;
+    int itmax = 0;
+    for (int v : it_h) {
+        ci += v;
+        itmax = std::max(itmax, v);
+    }
+    const double n = (double)c->n;
+    c->kt.bytes[0] += ci * n * 2.0 * es + itmax * n * 4.0 * rs;
+    c->kt.bytes[1] += ci * n * 6.0 * es + itmax * n * ds;
+    c->kt.bytes[2] += ci * n * 3.0 * es + itmax * n * ds;
+}
+
+// FP64 refinement residual r = b - A x on the columns still refining.
+int timed_ref_residual(dot_ctx* c, ElemKind ek64, const OpRaw& o64, int kp, const RefState& rs, const Launch& L) {
+    int act = kp;
+    if (c->timing) {
+        TRY(read_flag(c, rs.n_active, &act));
+        CK(cudaEventRecord(c->tev[32], c->s));
+    }
+    CK(ref_residual(ek64, o64, c->b64.p, c->x64.p, c->r64.p, c->n, kp, rs, c->rtol, L, c->s));
+    count(c, 1);
+    if (c->timing) {
+        CK(cudaEventRecord(c->tev[33], c->s));
+        CK(cudaEventSynchronize(c->tev[33]));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->tev[32], c->tev[33]));
+        c->kt.ms[3] += ms;
+        c->kt.launches[3] += 1;
+        const double es = esz64(c);
+        c->kt.bytes[3] += (double)act * c->n * 3.0 * es + (double)c->n * 4.0 * 8.0;
+    }
+    return DOT_OK;
+}
+
+int ensure_fields(dot_ctx* c) {
+    if (c->fields_valid) return DOT_OK;
+    TRY(ensure_coefficients(c));
+    if (c->ns == 0) return fail(DOT_ESTATE, "dot_set_sources has not been called");
+    if (c->nd == 0) return fail(DOT_ESTATE, "dot_set_detectors has not been called");
+    if (c->ls == 0 && c->ld == 0) return fail(DOT_ESTATE, "dot_set_sampling has not been called");
+    TRY(kp_limit_check(c));
+    const int kp = c->ls + c->ld;
+    const int64_t n = c->n;
+    const size_t nk = (size_t)n * kp;
+    const bool cx_ = cplx(c);
+    const ElemKind ek64 = cx_ ? EK_C128 : EK_F64;
+    const ElemKind ek32 = cx_ ? EK_C64 : EK_F32;
+    const Launch L = krylov_launch(n, kp, c->num_sms);
+    ColState st;
+    RefState rs;
+    TRY(alloc_colstate(c, kp, L, &st, &rs));
+    TRY(ensure(c->b64, nk * esz64(c)));
+    TRY(ensure(c->x64, nk * esz64(c)));
+    TRY(ensure(c->r64, nk * esz64(c)));
+    CK(cudaEventRecord(c->ev[0], c->s));
+    CK(build_rhs(cx_, c->rpB.as<int64_t>(), c->ciB.as<int32_t>(), c->vB.as<double>(), c->W.as<double>(), c->ns, c->ls,
+                 c->rpC.as<int64_t>(), c->ciC.as<int32_t>(), c->vC.as<double>(), c->V.as<double>(), c->nd, c->ld, n,
+                 c->b64.p, c->s));
+    count(c, 1);
+    CK(cudaEventRecord(c->ev[1], c->s));
+    const int maxit = c->maxit > 0 ? c->maxit : 10 * (c->nx + c->ny + c->nz);
+    std::vector<int> iters_tot(kp, 0), status(kp, 0), it_h(kp);
+    std::vector<double> rr(kp), bb(kp);
+    int outer = 0;
+    if (c->prec == DOT_PREC_FP64) {
+        TRY(ensure(c->p64, nk * esz64(c)));
+        TRY(ensure(c->q64, nk * esz64(c)));
+        const OpRaw o = op64(c);
+        CK(kry_init(ek64, o, c->b64.p, c->x64.p, c->r64.p, c->p64.p, n, kp, st, L, c->s));
+        int launched = 0;
+        TRY(krylov_loop(c, ek64, o, c->x64.p, c->r64.p, c->p64.p, c->q64.p, kp, st, c->rtol, maxit, L, &launched));
+        CK(cudaMemcpyAsync(it_h.data(), st.iters, kp * 4, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(status.data(), st.status, kp * 4, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(rr.data(), st.rr, kp * 8, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(bb.data(), st.bb, kp * 8, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        for (int j = 0; j < kp; ++j) iters_tot[j] = it_h[j];
+        account_bytes(c, it_h, esz64(c), 8, esz64(c));
+        count(c, 1);
+    } else {
+        TRY(ensure(c->x32, nk * esz32(c)));
+        TRY(ensure(c->r32, nk * esz32(c)));
+        TRY(ensure(c->p32, nk * esz32(c)));
+        TRY(ensure(c->q32, nk * esz32(c)));
+        const OpRaw o64 = op64(c), o32 = op32(c);
+        CK(ref_init(ek64, c->b64.p, c->x64.p, c->r64.p, n, kp, rs, L, c->s));
+        count(c, 1);
+        int act = 0;
+        for (outer = 0; outer < c->max_outer; ++outer) {
+            if (outer > 0) TRY(timed_ref_residual(c, ek64, o64, kp, rs, L));
+            TRY(read_flag(c, rs.n_active, &act));
+            if (act == 0) break;
+            CK(kry_init_from64(ek32, o32, c->r64.p, rs, c->x32.p, c->r32.p, c->p32.p, n, kp, st, L, c->s));
+            int launched = 0;
+            TRY(krylov_loop(c, ek32, o32, c->x32.p, c->r32.p, c->p32.p, c->q32.p, kp, st, c->inner_rtol, maxit, L,
+                            &launched));
+            CK(ref_promote(ek64, ek32, c->x64.p, c->x32.p, n, kp, rs, L, c->s));
+            CK(cudaMemcpyAsync(it_h.data(), st.iters, kp * 4, cudaMemcpyDeviceToHost, c->s));
+            CK(cudaStreamSynchronize(c->s));
+            for (int j = 0; j < kp; ++j) iters_tot[j] += it_h[j];
+            account_bytes(c, it_h, esz32(c), 4, esz32(c));
+            count(c, 2);
+        }
+        if (outer == c->max_outer) {
+            TRY(timed_ref_residual(c, ek64, o64, kp, rs, L));
+            TRY(read_flag(c, rs.n_active, &act));
+        }
+        CK(cudaMemcpyAsync(rr.data(), rs.rr, kp * 8, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(bb.data(), rs.bb, kp * 8, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        for (int j = 0; j < kp; ++j) {
+            const bool ok = bb[j] == 0.0 || (std::isfinite(rr[j]) && rr[j] <= c->rtol * c->rtol * bb[j]);
+            status[j] = ok ? DOT_OK : (std::isfinite(rr[j]) ? DOT_ENOTCONV : DOT_EBREAKDOWN);
+        }
+    }
+    CK(cudaEventRecord(c->ev[2], c->s));
+    CK(cudaEventSynchronize(c->ev[2]));
+    float ms_rhs = 0, ms_solve = 0;
+    cudaEventElapsedTime(&ms_rhs, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&ms_solve, c->ev[1], c->ev[2]);
+    int st_all = DOT_OK;
+    double relmax = 0.0;
+    int itmax = 0;
+    int64_t itsum = 0;
+    for (int j = 0; j < kp; ++j) {
+        if (status[j] == DOT_EBREAKDOWN) st_all = DOT_EBREAKDOWN;
+        else if (status[j] == DOT_ENOTCONV && st_all == DOT_OK) st_all = DOT_ENOTCONV;
+        if (bb[j] > 0) relmax = std::max(relmax, std::sqrt(rr[j] / bb[j]));
+        itmax = std::max(itmax, iters_tot[j]);
+        itsum += iters_tot[j];
+    }
+    c->stats.k = kp;
+    c->stats.iters_max = itmax;
+    c->stats.iters_sum = itsum;
+    c->stats.outer_steps = c->prec == DOT_PREC_FP64 ? 0 : outer;
+    c->stats.status = st_all;
+    c->stats.relres_max = relmax;
+    c->stats.columns_solved += kp;
+    c->stats.block_solves += 1;
+    c->stats.ms_setup = ms_rhs;
+    c->stats.ms_solve = ms_solve;
+    c->kp = kp;
+    c->fields_status = st_all;
+    c->fields_valid = true;
+    c->post_valid = false;
+    return DOT_OK;
+}
+
+int ensure_projection(dot_ctx* c) {
+    if (c->P_valid) return DOT_OK;
+    TRY(ensure(c->MW, (size_t)c->nd * std::max(c->ls, 1) * 16));
+    TRY(ensure(c->P, (size_t)std::max(c->ld, 1) * std::max(c->ls, 1) * 16));
+    CK(data_projection(cplx(c), c->M.as<double>(), c->nd, c->ns, c->W.as<double>(), c->ls, c->V.as<double>(), c->ld,
+                       c->MW.as<double>(), c->P.as<double>(), c->s));
+    count(c, 2);
+    c->P_valid = true;
+    return DOT_OK;
+}
+
+int ensure_post(dot_ctx* c) {
+    TRY(ensure_fields(c));
+    if (c->post_valid) return DOT_OK;
+    if (c->M_set) TRY(ensure_projection(c));
+    const size_t nr = (size_t)std::max(c->ls, 1) * std::max(c->ld, 1);
+    TRY(ensure(c->Tm, (size_t)c->nd * std::max(c->ls, 1) * 16));
+    TRY(ensure(c->S, nr * 16));
+    TRY(ensure(c->Rs, nr * 16));
+    TRY(ensure(c->f, 16));
+    CK(restriction_misfit(cplx(c), c->x64.p, c->kp, c->ls, c->cpC.as<int64_t>(), c->rwC.as<int32_t>(),
+                          c->vCc.as<double>(), c->nd, c->V.as<double>(), c->ld, c->P.as<double>(), c->M_set,
+                          c->Tm.as<double>(), c->S.as<double>(), c->Rs.as<double>(), c->f.as<double>(), c->s));
+    count(c, 2);
+    c->post_valid = true;
+    return DOT_OK;
+}
+
+// CSC (colptr, rows) -> CSR by voxel with the column index, on the host.
+void csc_to_csr(int64_t n, int ncol, const int64_t* colptr, const int32_t* rows, const double* vals,
+                std::vector<int64_t>& rp, std::vector<int32_t>& ci, std::vector<double>& cv) {
+    const int64_t nnz = colptr[ncol];
+    rp.assign(n + 1, 0);
+    for (int64_t t = 0; t < nnz; ++t) rp[rows[t] + 1]++;
+    for (int64_t v = 0; v < n; ++v) rp[v + 1] += rp[v];
+    ci.resize(nnz);
+    cv.resize(nnz);
+    std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
+    for (int col = 0; col < ncol; ++col)
+        for (int64_t t = colptr[col]; t < colptr[col + 1]; ++t) {
+            const int64_t dst = fill[rows[t]]++;
+            ci[dst] = col;
+            cv[dst] = vals[t];
+        }
+}
+
+int check_csc(const dot_ctx* c, int ncol, const int64_t* colptr, const int32_t* rows, const double* vals) {
+    if (ncol <= 0) return fail(DOT_EINVAL, "number of columns must be positive");
+    if (!colptr || (!rows && colptr[ncol] > 0) || (!vals && colptr[ncol] > 0))
+        return fail(DOT_EINVAL, "null CSC array");
+    if (colptr[0] != 0) return fail(DOT_EINVAL, "colptr[0] must be 0");
+    for (int j = 0; j < ncol; ++j)
+        if (colptr[j + 1] < colptr[j]) return fail(DOT_EINVAL, "colptr must be non-decreasing");
+    for (int64_t t = 0; t < colptr[ncol]; ++t)
+        if (rows[t] < 0 || rows[t] >= c->n) return fail(DOT_EINVAL, "row index out of range");
+    return DOT_OK;
+}
+
+int copy_out_complex_or_real(dot_ctx* c, const DevBuf& src, size_t count, double* host) {
+    // src holds `count` double2 values; real arithmetic returns the real parts only.
+    std::vector<double> tmp(count * 2);
+    CK(cudaMemcpyAsync(tmp.data(), src.p, count * 16, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if (cplx(c))
+        std::memcpy(host, tmp.data(), count * 16);
+    else
+        for (size_t t = 0; t < count; ++t) host[t] = tmp[2 * t];
+    return DOT_OK;
+}
+
+int set_pals_common(dot_ctx* c, int m0, double mu_in, double mu_out, double cut, double eps, double gamma) {
+    if (m0 <= 0) return fail(DOT_EINVAL, "m0 must be positive");
+    if (!(eps > 0.0)) return fail(DOT_EINVAL, "eps must be positive");
+    if (!(gamma >= 0.0)) return fail(DOT_EINVAL, "gamma must be non-negative");
+    c->m0 = m0;
+    c->mu_in = mu_in;
+    c->mu_out = mu_out;
+    c->cut = cut;
+    c->eps = eps;
+    c->gamma = gamma;
+    c->mu_mode = 2;
+    invalidate_coef(c);
+    return DOT_OK;
+}
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+const char* dot_last_error(void) { return g_err.c_str(); }
+
+int dot_create(dot_ctx** out, int device) {
+    if (!out) return fail(DOT_EINVAL, "null output pointer");
+    *out = nullptr;
+    int count = 0;
+    CK(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) return fail(DOT_EINVAL, "device ordinal out of range");
+    CK(cudaSetDevice(device));
+    dot_ctx* c = new dot_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_flag, sizeof(int));
+    for (int t = 0; t < 4 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->ev[t]);
+    for (int t = 0; t < 34 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->tev[t]);
+    if (e != cudaSuccess) {
+        dot_destroy(c);
+        return fail(DOT_ECUDA, std::string("context creation: ") + cudaGetErrorString(e));
+    }
+    c->s = c->own;
+    *out = c;
+    return DOT_OK;
+}
+
+int dot_destroy(dot_ctx* c) {
+    if (!c) return DOT_OK;
+    cudaSetDevice(c->device);
+    if (c->s) cudaStreamSynchronize(c->s);
+    DevBuf* bufs[] = {&c->D, &c->mu, &c->phi, &c->wdmu, &c->p, &c->cx, &c->cy, &c->cz, &c->dre, &c->dinv64,
+                      &c->cx32, &c->cy32, &c->cz32, &c->dre32, &c->dinv32, &c->rpB, &c->ciB, &c->vB, &c->rpC,
+                      &c->ciC, &c->vC, &c->cpC, &c->rwC, &c->vCc, &c->W, &c->V, &c->M, &c->MW, &c->P, &c->b64,
+                      &c->x64, &c->r64, &c->p64, &c->q64, &c->x32, &c->r32, &c->p32, &c->q32, &c->cs_rho,
+                      &c->cs_alpha, &c->cs_beta, &c->cs_rr, &c->cs_bb, &c->cs_active, &c->cs_iters, &c->cs_status,
+                      &c->cs_misc, &c->cs_partA, &c->cs_partB, &c->rs_bb, &c->rs_rr, &c->rs_scale, &c->rs_active,
+                      &c->rs_misc, &c->rs_partB, &c->Tm, &c->S, &c->Rs, &c->f, &c->gmu, &c->gp, &c->J, &c->tmp};
+    for (DevBuf* b : bufs) release(*b);
+    for (int t = 0; t < 4; ++t)
+        if (c->ev[t]) cudaEventDestroy(c->ev[t]);
+    for (int t = 0; t < 34; ++t)
+        if (c->tev[t]) cudaEventDestroy(c->tev[t]);
+    if (c->h_flag) cudaFreeHost(c->h_flag);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+    return DOT_OK;
+}
+
+int dot_set_stream(dot_ctx* c, void* stream) {
+    TRY(need_ctx(c));
+    CK(cudaStreamSynchronize(c->s));
+    c->s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    return DOT_OK;
+}
+
+int dot_set_grid(dot_ctx* c, int nx, int ny, int nz, double h, const int bc[6]) {
+    TRY(need_ctx(c));
+    if (nx < 1 || ny < 1 || nz < 1) return fail(DOT_EINVAL, "grid dimensions must be positive");
+    if ((int64_t)nx * ny * nz > (int64_t)1 << 31) return fail(DOT_EINVAL, "grid exceeds 2^31 cells");
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(DOT_EINVAL, "h must be positive and finite");
+    if (!bc) return fail(DOT_EINVAL, "null bc array");
+    for (int f = 0; f < 6; ++f)
+        if (bc[f] != DOT_BC_ROBIN && bc[f] != DOT_BC_DIRICHLET) return fail(DOT_EINVAL, "bad boundary flag");
+    const bool same_n = c->grid_set && (int64_t)nx * ny * nz == c->n;
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->h = h;
+    for (int f = 0; f < 6; ++f) c->bc[f] = bc[f];
+    c->n = (int64_t)nx * ny * nz;
+    c->grid_set = true;
+    if (!same_n) {
+        c->D_set = false;
+        if (c->mu_mode == 1) c->mu_mode = 0;
+        c->ns = c->nd = 0;
+    }
+    invalidate_coef(c);
+    return DOT_OK;
+}
+
+int dot_set_omega(dot_ctx* c, double w) {
+    TRY(need_ctx(c));
+    if (!std::isfinite(w)) return fail(DOT_EINVAL, "omega/nu must be finite");
+    if ((w != 0.0) != (c->w != 0.0)) c->P_valid = false;
+    c->w = w;
+    invalidate_coef(c);
+    return DOT_OK;
+}
+
+int dot_set_diffusion(dot_ctx* c, const double* D) {
+    TRY(need_grid(c));
+    if (!D) return fail(DOT_EINVAL, "null D");
+    for (int64_t v = 0; v < c->n; ++v)
+        if (!(D[v] > 0.0) || !std::isfinite(D[v])) return fail(DOT_EINVAL, "D must be positive and finite");
+    TRY(upload(c, c->D, D, c->n * 8));
+    c->D_set = true;
+    invalidate_coef(c);
+    return DOT_OK;
+}
+
+int dot_set_mua(dot_ctx* c, const double* mu) {
+    TRY(need_grid(c));
+    if (!mu) return fail(DOT_EINVAL, "null mu");
+    TRY(upload(c, c->mu, mu, c->n * 8));
+    c->mu_mode = 1;
+    invalidate_coef(c);
+    return DOT_OK;
+}
+
+int dot_set_pals(dot_ctx* c, int m0, const double* p, double mu_in, double mu_out, double cut, double eps,
+                 double gamma) {
+    TRY(need_grid(c));
+    if (!p) return fail(DOT_EINVAL, "null p");
+    TRY(set_pals_common(c, m0, mu_in, mu_out, cut, eps, gamma));
+    TRY(upload(c, c->p, p, (size_t)5 * m0 * 8));
+    return DOT_OK;
+}
+
+int dot_set_pals_dev(dot_ctx* c, int m0, const double* p_dev, double mu_in, double mu_out, double cut, double eps,
+                     double gamma) {
+    TRY(need_grid(c));
+    if (!p_dev) return fail(DOT_EINVAL, "null p");
+    TRY(set_pals_common(c, m0, mu_in, mu_out, cut, eps, gamma));
+    TRY(ensure(c->p, (size_t)5 * m0 * 8));
+    CK(cudaMemcpyAsync(c->p.p, p_dev, (size_t)5 * m0 * 8, cudaMemcpyDeviceToDevice, c->s));
+    return DOT_OK;
+}
+
+int dot_set_sources(dot_ctx* c, int ns, const int64_t* colptr, const int32_t* rows, const double* vals) {
+    TRY(need_grid(c));
+    TRY(check_csc(c, ns, colptr, rows, vals));
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<double> cv;
+    csc_to_csr(c->n, ns, colptr, rows, vals, rp, ci, cv);
+    TRY(upload(c, c->rpB, rp.data(), rp.size() * 8));
+    TRY(upload(c, c->ciB, ci.data(), ci.size() * 4));
+    TRY(upload(c, c->vB, cv.data(), cv.size() * 8));
+    if (ns != c->ns) {
+        c->ls = c->ld = 0;
+        c->M_set = false;
+    }
+    c->ns = ns;
+    c->P_valid = false;
+    invalidate_fields(c);
+    return DOT_OK;
+}
+
+int dot_set_detectors(dot_ctx* c, int nd, const int64_t* colptr, const int32_t* rows, const double* vals) {
+    TRY(need_grid(c));
+    TRY(check_csc(c, nd, colptr, rows, vals));
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<double> cv;
+    csc_to_csr(c->n, nd, colptr, rows, vals, rp, ci, cv);
+    TRY(upload(c, c->rpC, rp.data(), rp.size() * 8));
+    TRY(upload(c, c->ciC, ci.data(), ci.size() * 4));
+    TRY(upload(c, c->vC, cv.data(), cv.size() * 8));
+    TRY(upload(c, c->cpC, colptr, (size_t)(nd + 1) * 8));
+    TRY(upload(c, c->rwC, rows, (size_t)colptr[nd] * 4));
+    TRY(upload(c, c->vCc, vals, (size_t)colptr[nd] * 8));
+    if (nd != c->nd) {
+        c->ls = c->ld = 0;
+        c->M_set = false;
+    }
+    c->nd = nd;
+    c->P_valid = false;
+    invalidate_fields(c);
+    return DOT_OK;
+}
+
+int dot_set_data(dot_ctx* c, const double* M, int is_complex) {
+    TRY(need_ctx(c));
+    if (c->ns == 0 || c->nd == 0) return fail(DOT_ESTATE, "set sources and detectors before data");
+    if (!M) return fail(DOT_EINVAL, "null M");
+    const size_t cnt = (size_t)c->nd * c->ns;
+    std::vector<double> m2(cnt * 2, 0.0);
+    for (size_t t = 0; t < cnt; ++t) {
+        m2[2 * t] = is_complex ? M[2 * t] : M[t];
+        m2[2 * t + 1] = is_complex ? M[2 * t + 1] : 0.0;
+    }
+    TRY(upload(c, c->M, m2.data(), cnt * 16));
+    c->M_set = true;
+    c->P_valid = false;
+    c->post_valid = false;
+    return DOT_OK;
+}
+
+int dot_set_sampling(dot_ctx* c, int ls, const double* W, int ld, const double* V) {
+    TRY(need_ctx(c));
+    if (c->ns == 0 || c->nd == 0) return fail(DOT_ESTATE, "set sources and detectors before sampling");
+    if (ls < 1 || ld < 1) return fail(DOT_EINVAL, "ls and ld must be positive");
+    if (ls + ld > 1024) return fail(DOT_EINVAL, "ls + ld exceeds 1024");
+    if (!W || !V) return fail(DOT_EINVAL, "null W or V");
+    TRY(upload(c, c->W, W, (size_t)c->ns * ls * 8));
+    TRY(upload(c, c->V, V, (size_t)c->nd * ld * 8));
+    c->ls = ls;
+    c->ld = ld;
+    c->P_valid = false;
+    invalidate_fields(c);
+    return DOT_OK;
+}
+
+int dot_set_solver(dot_ctx* c, int precision, double rtol, int maxit) {
+    TRY(need_ctx(c));
+    if (precision != DOT_PREC_FP64 && precision != DOT_PREC_MIXED) return fail(DOT_EINVAL, "bad precision");
+    if (!(rtol > 0.0) || !(rtol < 1.0)) return fail(DOT_EINVAL, "rtol must lie in (0, 1)");
+    if (maxit < 0) return fail(DOT_EINVAL, "maxit must be non-negative");
+    c->prec = precision;
+    c->rtol = rtol;
+    c->maxit = maxit;
+    invalidate_fields(c);
+    return DOT_OK;
+}
+
+int dot_set_refinement(dot_ctx* c, double inner_rtol, int max_outer) {
+    TRY(need_ctx(c));
+    if (!(inner_rtol > 0.0) || !(inner_rtol < 1.0)) return fail(DOT_EINVAL, "inner_rtol must lie in (0, 1)");
+    if (max_outer < 1) return fail(DOT_EINVAL, "max_outer must be positive");
+    c->inner_rtol = inner_rtol;
+    c->max_outer = max_outer;
+    invalidate_fields(c);
+    return DOT_OK;
+}
+
+int dot_misfit(dot_ctx* c, double* f) {
+    TRY(need_grid(c));
+    if (!f) return fail(DOT_EINVAL, "null f");
+    if (!c->M_set) return fail(DOT_ESTATE, "dot_set_data has not been called");
+    TRY(ensure_post(c));
+    CK(cudaMemcpyAsync(f, c->f.p, 8, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if (c->fields_status != DOT_OK) return fail(c->fields_status, "block solve did not converge in every column");
+    return DOT_OK;
+}
+
+int dot_measurements(dot_ctx* c, double* S) {
+    TRY(need_grid(c));
+    if (!S) return fail(DOT_EINVAL, "null S");
+    TRY(ensure_post(c));
+    TRY(copy_out_complex_or_real(c, c->S, (size_t)c->ls * c->ld, S));
+    if (c->fields_status != DOT_OK) return fail(c->fields_status, "block solve did not converge in every column");
+    return DOT_OK;
+}
+
+int dot_gradient(dot_ctx* c, double* f, double* g) {
+    TRY(need_grid(c));
+    if (!f || !g) return fail(DOT_EINVAL, "null output");
+    if (!c->M_set) return fail(DOT_ESTATE, "dot_set_data has not been called");
+    TRY(ensure_post(c));
+    CK(cudaEventRecord(c->ev[3], c->s));
+    TRY(ensure(c->gmu, c->n * 8));
+    CK(sensitivity_gmu(cplx(c), c->x64.p, c->n, c->kp, c->ls, c->ld, c->Rs.as<double>(), c->gmu.as<double>(), c->s));
+    count(c, 1);
+    if (c->mu_mode == 2) {
+        TRY(ensure(c->gp, (size_t)5 * c->m0 * 8));
+        CK(pals_chain_gp(c->p.as<double>(), c->m0, c->gamma, c->nx, c->ny, c->nz, c->h, c->wdmu.as<double>(),
+                         c->gmu.as<double>(), c->gp.as<double>(), c->s));
+        count(c, 1);
+        CK(cudaMemcpyAsync(g, c->gp.p, (size_t)5 * c->m0 * 8, cudaMemcpyDeviceToHost, c->s));
+    } else {
+        CK(cudaMemcpyAsync(g, c->gmu.p, c->n * 8, cudaMemcpyDeviceToHost, c->s));
+    }
+    CK(cudaMemcpyAsync(f, c->f.p, 8, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaEventRecord(c->ev[2], c->s));
+    CK(cudaStreamSynchronize(c->s));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, c->ev[3], c->ev[2]);
+    c->stats.ms_post = ms;
+    if (c->fields_status != DOT_OK) return fail(c->fields_status, "block solve did not converge in every column");
+    return DOT_OK;
+}
+
+int dot_jacobian_mua(dot_ctx* c, double* J) {
+    TRY(need_grid(c));
+    if (!J) return fail(DOT_EINVAL, "null J");
+    TRY(ensure_fields(c));
+    const size_t cnt = (size_t)c->ls * c->ld * c->n;
+    TRY(ensure(c->J, cnt * esz64(c)));
+    CK(jacobian_mua(cplx(c), c->x64.p, c->n, c->kp, c->ls, c->ld, c->J.as<double>(), c->s));
+    CK(cudaMemcpyAsync(J, c->J.p, cnt * esz64(c), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if (c->fields_status != DOT_OK) return fail(c->fields_status, "block solve did not converge in every column");
+    return DOT_OK;
+}
+
+int dot_jacobian_p(dot_ctx* c, double* Jp) {
+    TRY(need_grid(c));
+    if (!Jp) return fail(DOT_EINVAL, "null Jp");
+    if (c->mu_mode != 2) return fail(DOT_ESTATE, "dot_jacobian_p needs dot_set_pals");
+    TRY(ensure_fields(c));
+    const size_t cnt = (size_t)c->ls * c->ld * 5 * c->m0;
+    TRY(ensure(c->J, cnt * esz64(c)));
+    CK(pals_chain_jp(cplx(c), c->p.as<double>(), c->m0, c->gamma, c->nx, c->ny, c->nz, c->h, c->wdmu.as<double>(),
+                     c->x64.p, c->kp, c->ls, c->ld, c->J.as<double>(), c->s));
+    CK(cudaMemcpyAsync(Jp, c->J.p, cnt * esz64(c), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if (c->fields_status != DOT_OK) return fail(c->fields_status, "block solve did not converge in every column");
+    return DOT_OK;
+}
+
+int dot_get_mua(dot_ctx* c, double* mu) {
+    TRY(need_grid(c));
+    if (!mu) return fail(DOT_EINVAL, "null mu");
+    TRY(ensure_coefficients(c));
+    CK(cudaMemcpyAsync(mu, c->mu.p, c->n * 8, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return DOT_OK;
+}
+
+int dot_get_fields(dot_ctx* c, double* U, double* Z) {
+    TRY(need_grid(c));
+    TRY(ensure_fields(c));
+    const size_t bytes = (size_t)c->n * std::max(c->ls, c->ld) * esz64(c);
+    TRY(ensure(c->tmp, bytes));
+    if (U) {
+        CK(blk_to_colmajor(cplx(c), c->x64.p, c->n, c->kp, 0, c->ls, c->tmp.as<double>(), c->s));
+        CK(cudaMemcpyAsync(U, c->tmp.p, (size_t)c->n * c->ls * esz64(c), cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+    }
+    if (Z) {
+        CK(blk_to_colmajor(cplx(c), c->x64.p, c->n, c->kp, c->ls, c->ld, c->tmp.as<double>(), c->s));
+        CK(cudaMemcpyAsync(Z, c->tmp.p, (size_t)c->n * c->ld * esz64(c), cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+    }
+    return DOT_OK;
+}
+
+int dot_get_stats(dot_ctx* c, dot_stats* out) {
+    if (!c || !out) return fail(DOT_EINVAL, "null argument");
+    *out = c->stats;
+    return DOT_OK;
+}
+
+int dot_set_kernel_timing(dot_ctx* c, int enable) {
+    TRY(need_ctx(c));
+    c->timing = enable != 0;
+    if (c->timing) c->kt = dot_kernel_timing{};
+    return DOT_OK;
+}
+
+int dot_get_kernel_timing(dot_ctx* c, dot_kernel_timing* out) {
+    if (!c || !out) return fail(DOT_EINVAL, "null argument");
+    *out = c->kt;
+    return DOT_OK;
+}
+
+int dot_apply(dot_ctx* c, int k, const double* x, double* y) {
+    TRY(need_grid(c));
+    if (k < 1 || !x || !y) return fail(DOT_EINVAL, "bad apply arguments");
+    TRY(ensure_coefficients(c));
+    const size_t bytes = (size_t)c->n * k * esz64(c);
+    DevBuf xin, xb, yb;
+    int rc = ensure(xin, bytes);
+    if (rc == DOT_OK) rc = ensure(xb, bytes);
+    if (rc == DOT_OK) rc = ensure(yb, bytes);
+    if (rc == DOT_OK) {
+        cudaError_t e = cudaMemcpyAsync(xin.p, x, bytes, cudaMemcpyHostToDevice, c->s);
+        if (e == cudaSuccess) e = blk_from_colmajor(cplx(c), xin.as<double>(), c->n, k, k, 0, xb.p, c->s);
+        if (e == cudaSuccess) e = op_apply(cplx(c) ? EK_C128 : EK_F64, op64(c), xb.p, yb.p, c->n, k, c->s);
+        if (e == cudaSuccess) e = blk_to_colmajor(cplx(c), yb.p, c->n, k, 0, k, xin.as<double>(), c->s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(y, xin.p, bytes, cudaMemcpyDeviceToHost, c->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+        if (e != cudaSuccess) rc = fail(DOT_ECUDA, std::string("dot_apply: ") + cudaGetErrorString(e));
+    }
+    release(xin);
+    release(xb);
+    release(yb);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// Shared device-side definitions of the DOT hot-path kernels (sm_103a).
+//
+// Element types: double (FP64, omega = 0), double2 (complex128), float (FP32),
+// float2 (complex64).  Block vectors are stored RHS-innermost: element (v, c) of a
+// block with kp columns lives at v * kp + c, so the k columns of one voxel are
+// contiguous and a warp reads consecutive columns of consecutive voxels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace dotk {
+
+// ------------------------------------------------------------------ element ops
+template <typename T> struct Elem;
+template <> struct Elem<float>   { using R = float;  static constexpr bool cplx = false; };
+template <> struct Elem<float2>  { using R = float;  static constexpr bool cplx = true;  };
+template <> struct Elem<double>  { using R = double; static constexpr bool cplx = false; };
+template <> struct Elem<double2> { using R = double; static constexpr bool cplx = true;  };
+
+template <typename T> __device__ __forceinline__ T ezero();
+template <> __device__ __forceinline__ float   ezero<float>()   { return 0.f; }
+template <> __device__ __forceinline__ double  ezero<double>()  { return 0.0; }
+template <> __device__ __forceinline__ float2  ezero<float2>()  { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 ezero<double2>() { return make_double2(0.0, 0.0); }
+
+__device__ __forceinline__ float   eadd(float a, float b)     { return a + b; }
+__device__ __forceinline__ double  eadd(double a, double b)   { return a + b; }
+__device__ __forceinline__ float2  eadd(float2 a, float2 b)   { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 eadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float   esub(float a, float b)     { return a - b; }
+__device__ __forceinline__ double  esub(double a, double b)   { return a - b; }
+__device__ __forceinline__ float2  esub(float2 a, float2 b)   { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 esub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float   emul(float a, float b)     { return a * b; }
+__device__ __forceinline__ double  emul(double a, double b)   { return a * b; }
+__device__ __forceinline__ float2  emul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 emul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// real scalar times element
+__device__ __forceinline__ float   escale(float s, float a)     { return s * a; }
+__device__ __forceinline__ double  escale(double s, double a)   { return s * a; }
+__device__ __forceinline__ float2  escale(float s, float2 a)    { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ double2 escale(double s, double2 a)  { return make_double2(s * a.x, s * a.y); }
+// i * w * a (complex only; real types never carry a frequency term)
+__device__ __forceinline__ float   emul_i(float, float)          { return 0.f; }
+__device__ __forceinline__ double  emul_i(double, double)        { return 0.0; }
+__device__ __forceinline__ float2  emul_i(float w, float2 a)     { return make_float2(-w * a.y, w * a.x); }
+__device__ __forceinline__ double2 emul_i(double w, double2 a)   { return make_double2(-w * a.y, w * a.x); }
+// |a|^2
+__device__ __forceinline__ float   eabs2(float a)   { return a * a; }
+__device__ __forceinline__ double  eabs2(double a)  { return a * a; }
+__device__ __forceinline__ float   eabs2(float2 a)  { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double  eabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+// widen to a complex double pair (real part only for real types)
+__device__ __forceinline__ double2 ewide(float a)   { return make_double2((double)a, 0.0); }
+__device__ __forceinline__ double2 ewide(double a)  { return make_double2(a, 0.0); }
+__device__ __forceinline__ double2 ewide(float2 a)  { return make_double2((double)a.x, (double)a.y); }
+__device__ __forceinline__ double2 ewide(double2 a) { return a; }
+// narrow a complex double scalar to the element type
+template <typename T> __device__ __forceinline__ T enarrow(double2 s);
+template <> __device__ __forceinline__ float   enarrow<float>(double2 s)   { return (float)s.x; }
+template <> __device__ __forceinline__ double  enarrow<double>(double2 s)  { return s.x; }
+template <> __device__ __forceinline__ float2  enarrow<float2>(double2 s)  { return make_float2((float)s.x, (float)s.y); }
+template <> __device__ __forceinline__ double2 enarrow<double2>(double2 s) { return s; }
+
+// complex-double scalar arithmetic used by the per-column finalisers
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+    // Smith's algorithm (R. L. Smith, CACM 5(8), 1962) to avoid overflow
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, den = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+    }
+    double r = b.x / b.y, den = b.x * r + b.y;
+    return make_double2((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+}
+__device__ __forceinline__ bool zfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// ---------------------------------------------------------------- operator
+// Coefficients of (A(mu) + i w I), per unit volume:
+//   (A u)_v = dre_v u_v + i w u_v - sum_faces cf * u_nb
+// cx[v] couples v and v+1 (0 on the +x boundary), cy[v] v and v+nx, cz[v] v and v+nx*ny.
+// dinv = 1 / (dre + i w) is the Jacobi preconditioner, stored in the element type.
+template <typename T>
+struct Op {
+    using R = typename Elem<T>::R;
+    const R* cx;
+    const R* cy;
+    const R* cz;
+    const R* dre;
+    const T* dinv;
+    R w;
+    int nx, ny, nz;
+};
+
+// y = A x at voxel v, column c of a block with kp columns.
+template <typename T>
+__device__ __forceinline__ T apply_at(const Op<T>& op, const T* __restrict__ x, int64_t v, int kp, int c) {
+    using R = typename Elem<T>::R;
+    const int64_t nxy = (int64_t)op.nx * op.ny;
+    const int i = (int)(v % op.nx);
+    const int j = (int)((v / op.nx) % op.ny);
+    const int kz = (int)(v / nxy);
+    const int64_t e = v * kp + c;
+    T xc = x[e];
+    T acc = escale(op.dre[v], xc);
+    if (Elem<T>::cplx) acc = eadd(acc, emul_i(op.w, xc));
+    if (i > 0)          acc = esub(acc, escale(op.cx[v - 1], x[e - kp]));
+    if (i < op.nx - 1)  acc = esub(acc, escale(op.cx[v], x[e + kp]));
+    if (j > 0)          acc = esub(acc, escale(op.cy[v - op.nx], x[e - (int64_t)op.nx * kp]));
+    if (j < op.ny - 1)  acc = esub(acc, escale(op.cy[v], x[e + (int64_t)op.nx * kp]));
+    if (kz > 0)         acc = esub(acc, escale(op.cz[v - nxy], x[e - nxy * kp]));
+    if (kz < op.nz - 1) acc = esub(acc, escale(op.cz[v], x[e + nxy * kp]));
+    (void)sizeof(R);
+    return acc;
+}
+
+}  // namespace dotk

@@ -1,0 +1,30 @@
+"""Test helper: configure a library context from a synthetic problem (C ABI calls only)."""
+import numpy as np
+
+from paper_1706_05586_gb300 import dot as D
+from paper_1706_05586_gb300 import synth
+
+
+def configure(ctx, pb, *, p=None, mua=None, prec=D.PREC_FP64, rtol=1e-13, maxit=0, W=None, V=None,
+              data=True):
+    wl = pb.wl
+    D.dot_set_grid(ctx, wl.nx, wl.ny, wl.nz, wl.h, wl.bc)
+    D.dot_set_omega(ctx, wl.omega_nu)
+    D.dot_set_diffusion(ctx, pb.D)
+    if mua is not None:
+        D.dot_set_mua(ctx, mua)
+    else:
+        D.dot_set_pals(ctx, pb.inp.p0 if p is None else p, synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps,
+                       wl.gamma)
+    D.dot_set_sources(ctx, pb.inp.B)
+    D.dot_set_detectors(ctx, pb.inp.C)
+    if data:
+        D.dot_set_data(ctx, pb.M)
+    D.dot_set_sampling(ctx, pb.inp.W if W is None else W, pb.inp.V if V is None else V)
+    D.dot_set_solver(ctx, prec, rtol, maxit)
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    den = np.linalg.norm(b.ravel())
+    return np.linalg.norm((a - b).ravel()) / (den if den > 0 else 1.0)

@@ -1,0 +1,221 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
+seeded inputs.
+
+FP64 path: both sides solve to rtol 1e-13 and every output must agree to 1e-10
+relative (Frobenius norm of the difference over the norm of the oracle value).
+Mixed precision (FP32 / complex64 Krylov inside FP64 refinement to rtol 1e-11):
+1e-8 relative.  The misfit is compared as |df| / max(f, 1e-4 ||V^T M W||_F^2)
+because f is a difference of nearly equal terms near the true parameters.
+"""
+import numpy as np
+import pytest
+
+from oracle import dot_oracle as orc
+from paper_1706_05586_gb300 import dot as D
+from paper_1706_05586_gb300 import synth
+from tests import problem
+from tests.gpu_setup import configure, rel
+
+pytestmark = pytest.mark.gpu
+
+ROB, DIR = synth.ROBIN, synth.DIRICHLET
+
+CASES = {
+    # odd shape, the paper's boundary setting (Dirichlet laterally, Robin top and bottom)
+    "real_9x7x5_mixedbc": synth.small_workload(9, 7, 5, 0.4, src_grid=(2, 2), det_grid=(2, 1), ls=2, ld=1, m0=4,
+                                               bc=(DIR, DIR, DIR, DIR, ROB, ROB), seed_index=61),
+    # complex (COCG), ragged sizes, Gaussian sampling
+    "cplx_11x6x7": synth.small_workload(11, 6, 7, 0.35, omega_nu=0.3, src_grid=(3, 1), det_grid=(2, 2), ls=3, ld=2,
+                                        m0=5, sampling="gaussian", seed_index=62),
+    # single simultaneous source and detector
+    "real_13x10x6_l1": synth.small_workload(13, 10, 6, 0.3, src_grid=(3, 2), det_grid=(2, 3), ls=1, ld=1, m0=3,
+                                            seed_index=63),
+    # the 32x32x16 workload (16,384 cells, 27 RBFs, 2 + 2 Rademacher columns)
+    "dot32x32x16": synth.WORKLOADS["dot32x32x16"],
+    # the 100 MHz frequency on a 24x20x12 grid
+    "cplx_24x20x12_100MHz": synth.small_workload(24, 20, 12, 0.25, omega_nu=synth.OMEGA_NU_100MHZ, src_grid=(3, 3),
+                                                 det_grid=(3, 3), ls=4, ld=4, m0=8, sampling="gaussian",
+                                                 seed_index=64, rbf_radius=1.0),
+}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    h = D.dot_create(0)
+    yield h
+    D.dot_destroy(h)
+
+
+_cache = {}
+
+
+def _case(name):
+    if name not in _cache:
+        pb = problem.build(CASES[name])
+        _cache[name] = (pb, pb.evaluate(pb.inp.p0))
+    return _cache[name]
+
+
+def _cplx(pb):
+    return pb.wl.omega_nu != 0.0
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_stencil_apply(name, ctx):
+    pb, _ = _case(name)
+    mu = pb.mu_of(pb.inp.p0)
+    configure(ctx, pb, mua=mu)
+    A = pb.A_of(mu)
+    rng = np.random.default_rng(5)
+    for k in (1, 3):
+        X = rng.standard_normal((pb.wl.n, k))
+        if _cplx(pb):
+            X = X + 1j * rng.standard_normal((pb.wl.n, k))
+        Y = D.dot_apply(ctx, X, _cplx(pb))
+        ref = A @ X
+        assert np.max(np.abs(Y - ref)) <= 1e-14 * np.max(np.abs(ref)), name
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_pals_absorption(name, ctx):
+    pb, _ = _case(name)
+    configure(ctx, pb, p=pb.inp.p0)
+    mu = D.dot_get_mua(ctx, pb.wl.n)
+    assert np.max(np.abs(mu - pb.mu_of(pb.inp.p0))) <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_misfit_gradient_fp64(name, ctx):
+    pb, ref = _case(name)
+    configure(ctx, pb, p=pb.inp.p0)
+    f, g, rc = D.dot_gradient(ctx, pb.wl.np_)
+    assert rc == D.DOT_OK
+    P = pb.inp.V.T @ pb.M @ pb.inp.W
+    assert abs(f - ref["f"]) <= 1e-10 * max(ref["f"], 1e-4 * np.sum(np.abs(P) ** 2))
+    assert rel(g, ref["g_p"]) <= 1e-10, (g, ref["g_p"])
+    S, _ = D.dot_measurements(ctx, pb.wl.ls, pb.wl.ld, _cplx(pb))
+    assert rel(S, ref["S"]) <= 1e-10
+    st = D.dot_get_stats(ctx)
+    assert st["k"] == pb.wl.ls + pb.wl.ld and st["relres_max"] <= 1e-13
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fields_and_jacobians_fp64(name, ctx):
+    pb, ref = _case(name)
+    configure(ctx, pb, p=pb.inp.p0)
+    U, Z = D.dot_get_fields(ctx, pb.wl.n, pb.wl.ls, pb.wl.ld, _cplx(pb))
+    assert rel(U, ref["Uf"] @ pb.inp.W) <= 1e-10
+    assert rel(Z, ref["Zf"] @ pb.inp.V) <= 1e-10
+    Jmu, _ = D.dot_jacobian_mua(ctx, pb.wl.ls, pb.wl.ld, pb.wl.n, _cplx(pb))
+    assert rel(Jmu, ref["J_mu"]) <= 1e-10
+    Jp, _ = D.dot_jacobian_p(ctx, pb.wl.ls, pb.wl.ld, pb.wl.np_, _cplx(pb))
+    assert rel(Jp, ref["J_p"]) <= 1e-10
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_gradient_wrt_mua(name, ctx):
+    pb, _ = _case(name)
+    mu = pb.mu_of(pb.inp.p0)
+    configure(ctx, pb, mua=mu)
+    f, g, _ = D.dot_gradient(ctx, pb.wl.n)
+    ref = orc.evaluate(pb.D, mu, pb.grid, pb.wl.bc, pb.wl.omega_nu, pb.Bd, pb.Cd, pb.M, pb.inp.W, pb.inp.V)
+    assert rel(g, ref["g_mu"]) <= 1e-10
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_precision(name, ctx):
+    pb, ref = _case(name)
+    configure(ctx, pb, p=pb.inp.p0, prec=D.PREC_MIXED, rtol=1e-11)
+    f, g, rc = D.dot_gradient(ctx, pb.wl.np_)
+    assert rc == D.DOT_OK
+    st = D.dot_get_stats(ctx)
+    assert st["relres_max"] <= 1e-11 and st["outer_steps"] >= 2
+    P = pb.inp.V.T @ pb.M @ pb.inp.W
+    assert abs(f - ref["f"]) <= 1e-8 * max(ref["f"], 1e-4 * np.sum(np.abs(P) ** 2))
+    assert rel(g, ref["g_p"]) <= 1e-8
+    S, _ = D.dot_measurements(ctx, pb.wl.ls, pb.wl.ld, _cplx(pb))
+    assert rel(S, ref["S"]) <= 1e-8
+
+
+def test_gradient_at_true_parameters(ctx):
+    """Near p_true the misfit is noise-sized; the gradient is checked against the scale
+    2 ||J_p|| ||R_s|| that bounds it."""
+    pb, _ = _case("dot32x32x16")
+    ref = pb.evaluate(pb.inp.p_true)
+    configure(ctx, pb, p=pb.inp.p_true)
+    f, g, _ = D.dot_gradient(ctx, pb.wl.np_)
+    scale = 2 * np.linalg.norm(ref["J_p"]) * np.linalg.norm(ref["R_s"])
+    assert np.linalg.norm(g - ref["g_p"]) <= 1e-10 * scale
+    P = pb.inp.V.T @ pb.M @ pb.inp.W
+    assert abs(f - ref["f"]) <= 1e-10 * max(ref["f"], 1e-4 * np.sum(np.abs(P) ** 2))
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_zero_column_and_determinism(ctx):
+    pb, ref = _case("cplx_11x6x7")
+    W = pb.inp.W.copy()
+    W[:, 1] = 0.0                       # a simultaneous source with no light
+    configure(ctx, pb, p=pb.inp.p0, W=W)
+    f1, g1, rc = D.dot_gradient(ctx, pb.wl.np_)
+    assert rc == D.DOT_OK
+    S, _ = D.dot_measurements(ctx, pb.wl.ls, pb.wl.ld, True)
+    assert np.all(S[:, 1] == 0)
+    D.dot_set_solver(ctx, D.PREC_FP64, 1e-13, 0)   # invalidates the solve
+    f2, g2, _ = D.dot_gradient(ctx, pb.wl.np_)
+    assert f1 == f2 and np.array_equal(g1, g2)
+
+
+def test_cache_reuse_and_invalidation(ctx):
+    pb, _ = _case("real_9x7x5_mixedbc")
+    configure(ctx, pb, p=pb.inp.p0)
+    D.dot_gradient(ctx, pb.wl.np_)
+    n0 = D.dot_get_stats(ctx)["block_solves"]
+    D.dot_misfit(ctx)
+    D.dot_gradient(ctx, pb.wl.np_)
+    assert D.dot_get_stats(ctx)["block_solves"] == n0
+    D.dot_set_pals(ctx, pb.inp.p_true, synth.MU_IN, synth.MU_OUT, pb.wl.cutoff, pb.wl.eps, pb.wl.gamma)
+    D.dot_gradient(ctx, pb.wl.np_)
+    assert D.dot_get_stats(ctx)["block_solves"] == n0 + 1
+
+
+def test_not_converged_reports_status(ctx):
+    pb, _ = _case("dot32x32x16")
+    configure(ctx, pb, p=pb.inp.p0, maxit=3)
+    f, rc = D.dot_misfit(ctx, allow=(D.DOT_ENOTCONV,))
+    assert rc == D.DOT_ENOTCONV and np.isfinite(f)
+    assert D.dot_get_stats(ctx)["iters_max"] == 3
+    D.dot_set_solver(ctx, D.PREC_FP64, 1e-10, 0)
+    f, rc = D.dot_misfit(ctx)
+    assert rc == D.DOT_OK
+
+
+def test_argument_and_state_errors(ctx):
+    h = D.dot_create(0)
+    try:
+        with pytest.raises(D.DotError) as e:
+            D.dot_misfit(h)
+        assert e.value.code == D.DOT_ESTATE
+        with pytest.raises(D.DotError) as e:
+            D.dot_set_grid(h, 4, 4, 0, 0.1, (0,) * 6)
+        assert e.value.code == D.DOT_EINVAL
+        with pytest.raises(D.DotError) as e:
+            D.dot_set_grid(h, 4, 4, 4, 0.1, (0, 0, 7, 0, 0, 0))
+        assert e.value.code == D.DOT_EINVAL
+        D.dot_set_grid(h, 4, 4, 4, 0.1, (0,) * 6)
+        with pytest.raises(D.DotError) as e:
+            D.dot_set_diffusion(h, -np.ones(64))
+        assert e.value.code == D.DOT_EINVAL
+        with pytest.raises(D.DotError) as e:
+            D.dot_set_sources(h, (np.array([0, 1]), np.array([64]), np.array([1.0])))
+        assert e.value.code == D.DOT_EINVAL
+        D.dot_set_sources(h, (np.array([0, 1]), np.array([3]), np.array([1.0])))
+        D.dot_set_detectors(h, (np.array([0, 1]), np.array([60]), np.array([1.0])))
+        with pytest.raises(D.DotError) as e:
+            D.dot_set_sampling(h, np.ones((1, 600)), np.ones((1, 600)))
+        assert e.value.code == D.DOT_EINVAL
+        with pytest.raises(D.DotError) as e:
+            D.dot_misfit(h)
+        assert e.value.code == D.DOT_ESTATE
+    finally:
+        D.dot_destroy(h)
