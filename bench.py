@@ -154,10 +154,9 @@ def setup_problem(D, ctx, wl, inp, prec, rtol, log):
     D.dot_set_sources(ctx, inp.B)
     D.dot_set_detectors(ctx, inp.C)
     t0 = time.perf_counter()
-    D.dot_set_sampling(ctx, np.eye(wl.ns), np.eye(wl.nd))
     D.dot_set_solver(ctx, D.PREC_MIXED, 1e-10, 0)
-    Mclean, _ = D.dot_measurements(ctx, wl.ns, wl.nd, wl.omega_nu != 0.0)
-    log(f"data synthesis ({wl.ns}+{wl.nd} columns): {time.perf_counter() - t0:.1f} s")
+    Mclean, _ = D.dot_forward_model(ctx, wl.ns, wl.nd, wl.omega_nu != 0.0)
+    log(f"data synthesis ({wl.ns} source columns): {time.perf_counter() - t0:.1f} s")
     M = synth.add_noise(Mclean, inp)
     D.dot_set_data(ctx, M)
     D.dot_set_sampling(ctx, inp.W, inp.V)
@@ -220,6 +219,7 @@ def run_ours(args):
     clocks.start()
     D.dot_set_kernel_timing(ctx, 1)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()   # ncu --profile-from-start off captures the timed steps only
     ev0.record(stream)
     for k in range(args.warmup, args.warmup + args.steps):
         f, g, _ = step(k)
@@ -227,6 +227,7 @@ def run_ours(args):
         iters.append((st["iters_max"], st["outer_steps"], st["relres_max"]))
     ev1.record(stream)
     barrier()
+    torch.cuda.profiler.stop()
     D.dot_set_kernel_timing(ctx, 0)
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)

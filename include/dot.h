@@ -157,6 +157,12 @@ int dot_misfit(dot_ctx* ctx, double* f);
  * complex interleaved when omega != 0); with W = I, V = I this is the full
  * C^T A^{-1} B of Eq. (Eq:compmeas).  Does not need data. */
 int dot_measurements(dot_ctx* ctx, double* S);
+/* Computed measurements of every physical source, C^T A^{-1} B (nd x ns,
+ * column-major; complex interleaved when omega != 0): Eq. (Eq:compmeas) for all
+ * b_i.  Solves the ns source columns in blocks of 64 with the current solver
+ * settings; needs no sampling and no data, and leaves the sampled state as it was
+ * (the next evaluation solves again). */
+int dot_forward_model(dot_ctx* ctx, double* M);
 /* f and its gradient: g (5*m0 doubles) with respect to p after dot_set_pals,
  * or (N doubles) with respect to mu after dot_set_mua.  g = 2 Re J^T conj(vec R_s)
  * with J the sampled Jacobian of Eq. (Jacobian kth column). */

@@ -813,6 +813,73 @@ int dot_gradient(dot_ctx* c, double* f, double* g) {
     return DOT_OK;
 }
 
+int dot_forward_model(dot_ctx* c, double* M) {
+    TRY(need_grid(c));
+    if (!M) return fail(DOT_EINVAL, "null M");
+    if (c->ns == 0 || c->nd == 0) return fail(DOT_ESTATE, "set sources and detectors first");
+    TRY(ensure_coefficients(c));
+    const int chunk = 64;
+    DevBuf saveW = c->W;
+    const int save_ls = c->ls, save_ld = c->ld;
+    DevBuf Wc;
+    int rc = ensure(Wc, (size_t)c->ns * chunk * 8);
+    int worst = DOT_OK;
+    std::vector<double> hw((size_t)c->ns * chunk), ht;
+    for (int s0 = 0; rc == DOT_OK && s0 < c->ns; s0 += chunk) {
+        const int cw = std::min(chunk, c->ns - s0);
+        std::fill(hw.begin(), hw.end(), 0.0);
+        for (int i = 0; i < cw; ++i) hw[(size_t)(s0 + i) + (size_t)c->ns * i] = 1.0;
+        c->W = Wc;
+        c->ls = cw;
+        c->ld = 0;
+        invalidate_fields(c);
+        rc = upload(c, Wc, hw.data(), (size_t)c->ns * cw * 8);
+        if (rc == DOT_OK) rc = ensure_fields(c);
+        if (rc == DOT_OK) {
+            if (c->fields_status != DOT_OK && worst == DOT_OK) worst = c->fields_status;
+            rc = ensure(c->Tm, (size_t)c->nd * cw * 16);
+            if (rc == DOT_OK) rc = ensure(c->S, 16);
+            if (rc == DOT_OK) rc = ensure(c->Rs, 16);
+            if (rc == DOT_OK) rc = ensure(c->f, 16);
+        }
+        if (rc == DOT_OK) {
+            // T = C^T U for this chunk of physical sources (the V projection is empty)
+            cudaError_t e = restriction_misfit(cplx(c), c->x64.p, c->kp, cw, c->cpC.as<int64_t>(),
+                                               c->rwC.as<int32_t>(), c->vCc.as<double>(), c->nd, nullptr, 0,
+                                               nullptr, false, c->Tm.as<double>(), c->S.as<double>(),
+                                               c->Rs.as<double>(), c->f.as<double>(), c->s);
+            count(c, 2);
+            ht.resize((size_t)c->nd * cw * 2);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(ht.data(), c->Tm.p, (size_t)c->nd * cw * 16, cudaMemcpyDeviceToHost, c->s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+            if (e != cudaSuccess) {
+                rc = fail(DOT_ECUDA, std::string("dot_forward_model: ") + cudaGetErrorString(e));
+                break;
+            }
+            for (int i = 0; i < cw; ++i)
+                for (int d = 0; d < c->nd; ++d) {
+                    const size_t src = (size_t)d + (size_t)c->nd * i;
+                    const size_t dst = (size_t)d + (size_t)c->nd * (s0 + i);
+                    if (cplx(c)) {
+                        M[2 * dst] = ht[2 * src];
+                        M[2 * dst + 1] = ht[2 * src + 1];
+                    } else {
+                        M[dst] = ht[2 * src];
+                    }
+                }
+        }
+    }
+    c->W = saveW;
+    c->ls = save_ls;
+    c->ld = save_ld;
+    invalidate_fields(c);
+    release(Wc);
+    if (rc != DOT_OK) return rc;
+    if (worst != DOT_OK) return fail(worst, "a forward solve did not converge");
+    return DOT_OK;
+}
+
 int dot_jacobian_mua(dot_ctx* c, double* J) {
     TRY(need_grid(c));
     if (!J) return fail(DOT_EINVAL, "null J");

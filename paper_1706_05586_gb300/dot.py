@@ -48,6 +48,7 @@ SIGNATURES = {
     "dot_set_refinement": [C.c_void_p, C.c_double, C.c_int],
     "dot_misfit": [C.c_void_p, C.c_void_p],
     "dot_measurements": [C.c_void_p, C.c_void_p],
+    "dot_forward_model": [C.c_void_p, C.c_void_p],
     "dot_gradient": [C.c_void_p, C.c_void_p, C.c_void_p],
     "dot_jacobian_mua": [C.c_void_p, C.c_void_p],
     "dot_jacobian_p": [C.c_void_p, C.c_void_p],
@@ -220,6 +221,12 @@ def dot_measurements(ctx, ls, ld, cplx, allow=()):
     S = np.zeros((ld, ls), dtype=np.complex128 if cplx else np.float64, order="F")
     rc = _check(load().dot_measurements(ctx, _ptr(S)), allow)
     return S, rc
+
+
+def dot_forward_model(ctx, ns, nd, cplx, allow=()):
+    M = np.zeros((nd, ns), dtype=np.complex128 if cplx else np.float64, order="F")
+    rc = _check(load().dot_forward_model(ctx, _ptr(M)), allow)
+    return M, rc
 
 
 def dot_gradient(ctx, ng, allow=()):

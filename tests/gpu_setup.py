@@ -28,3 +28,12 @@ def rel(a, b):
     a, b = np.asarray(a), np.asarray(b)
     den = np.linalg.norm(b.ravel())
     return np.linalg.norm((a - b).ravel()) / (den if den > 0 else 1.0)
+
+
+def grad_err(g, ref_g, J, R_s, S):
+    """Gradient error over 2 ||J|| (||R_s|| + ||S||): the first-order size of the change of
+    g = 2 Re J^T conj(R_s) under relative perturbations of J and of S (R_s = S - V^T M W, so
+    near the data R_s is a difference of nearly equal terms and its own relative error is
+    amplified by ||S|| / ||R_s||)."""
+    scale = 2.0 * np.linalg.norm(J) * (np.linalg.norm(R_s) + np.linalg.norm(S))
+    return float(np.linalg.norm(np.asarray(g) - np.asarray(ref_g)) / scale)

@@ -1,0 +1,91 @@
+"""Parity at the full 1,048,576-cell frequency-domain workload, in the launch
+configuration the benchmark times (complex64 COCG inside FP64 refinement to
+relative residual 1e-10, 32 + 32 columns).  The oracle cannot evaluate the whole
+workload here, so it checks what it can compute one by one, and properties that
+hold at any size:
+  * the true FP64 residual ||BW - A U|| / ||BW|| of every column, with A assembled
+    by the oracle;
+  * one forward column solved by the oracle's own COCG, and the measurements
+    S[:, 0] = (CV)^T U_0 it implies;
+  * the gradient against a central difference of the GPU misfit along a random
+    direction (a property of any correct gradient).
+"""
+import numpy as np
+import pytest
+
+from oracle import dot_oracle as orc
+from paper_1706_05586_gb300 import dot as D
+from paper_1706_05586_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+WL = synth.WORKLOADS["dot128x128x64_w100MHz"]
+
+
+@pytest.fixture(scope="module")
+def setup():
+    inp = synth.draw(WL)
+    X = orc.cell_centres(WL.nx, WL.ny, WL.nz, WL.h)
+    kw = dict(mu_in=synth.MU_IN, mu_out=synth.MU_OUT, c=WL.cutoff, eps=WL.eps, gamma=WL.gamma)
+    Dfield = synth.diffusion_from_mua(orc.pals_mu(inp.p_true, X, **kw))
+    mu0 = orc.pals_mu(inp.p0, X, **kw)
+    A = orc.assemble(Dfield, mu0, WL.nx, WL.ny, WL.nz, WL.h, WL.bc, WL.omega_nu)
+    B = orc.sparse_of_csc(WL.n, inp.B)
+    C = orc.sparse_of_csc(WL.n, inp.C)
+    rng = np.random.default_rng(3)
+    M = (rng.standard_normal((WL.nd, WL.ns)) + 1j * rng.standard_normal((WL.nd, WL.ns))) * 1e-6
+    h = D.dot_create(0)
+    D.dot_set_grid(h, WL.nx, WL.ny, WL.nz, WL.h, WL.bc)
+    D.dot_set_omega(h, WL.omega_nu)
+    D.dot_set_diffusion(h, Dfield)
+    D.dot_set_pals(h, inp.p0, synth.MU_IN, synth.MU_OUT, WL.cutoff, WL.eps, WL.gamma)
+    D.dot_set_sources(h, inp.B)
+    D.dot_set_detectors(h, inp.C)
+    D.dot_set_data(h, M)
+    D.dot_set_sampling(h, inp.W, inp.V)
+    D.dot_set_solver(h, D.PREC_MIXED, 1e-10, 0)
+    f, g, rc = D.dot_gradient(h, WL.np_)
+    assert rc == D.DOT_OK
+    yield dict(h=h, inp=inp, A=A, B=B, C=C, mu0=mu0, f=f, g=g, st=D.dot_get_stats(h))
+    D.dot_destroy(h)
+
+
+def test_absorption_matches(setup):
+    mu = D.dot_get_mua(setup["h"], WL.n)
+    assert np.max(np.abs(mu - setup["mu0"])) <= 1e-12
+
+
+def test_true_residual_every_column(setup):
+    h, inp, A = setup["h"], setup["inp"], setup["A"]
+    U, Z = D.dot_get_fields(h, WL.n, WL.ls, WL.ld, True)
+    for X, R in ((U, setup["B"] @ inp.W), (Z, setup["C"] @ inp.V)):
+        res = np.linalg.norm(R - A @ X, axis=0) / np.linalg.norm(R, axis=0)
+        assert np.all(res <= 1.5e-10), res.max()
+    assert setup["st"]["relres_max"] <= 1e-10
+
+
+def test_one_column_against_oracle_solve(setup):
+    h, inp, A = setup["h"], setup["inp"], setup["A"]
+    b0 = setup["B"] @ inp.W[:, 0]
+    u0, _ = orc.krylov_solve(A, b0.astype(complex), rtol=1e-12)
+    U, _ = D.dot_get_fields(h, WL.n, WL.ls, WL.ld, True)
+    assert np.linalg.norm(U[:, 0] - u0) <= 1e-8 * np.linalg.norm(u0)
+    S, _ = D.dot_measurements(h, WL.ls, WL.ld, True)
+    s_ref = (setup["C"] @ inp.V).T @ u0
+    assert np.linalg.norm(S[:, 0] - s_ref) <= 1e-8 * np.linalg.norm(s_ref)
+
+
+def test_gradient_directional_difference(setup):
+    h, inp = setup["h"], setup["inp"]
+    rng = np.random.default_rng(11)
+    d = rng.standard_normal(WL.np_)
+    d[1::5] = 0.0
+    d /= np.linalg.norm(d)
+    eps = 1e-4
+    fs = []
+    for s in (+1, -1):
+        D.dot_set_pals(h, inp.p0 + s * eps * d, synth.MU_IN, synth.MU_OUT, WL.cutoff, WL.eps, WL.gamma)
+        fs.append(D.dot_misfit(h)[0])
+    fd = (fs[0] - fs[1]) / (2 * eps)
+    gd = float(setup["g"] @ d)
+    assert abs(fd - gd) <= 1e-5 * np.linalg.norm(setup["g"]), (fd, gd)

@@ -1,11 +1,16 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
 seeded inputs.
 
-FP64 path: both sides solve to rtol 1e-13 and every output must agree to 1e-10
-relative (Frobenius norm of the difference over the norm of the oracle value).
-Mixed precision (FP32 / complex64 Krylov inside FP64 refinement to rtol 1e-11):
-1e-8 relative.  The misfit is compared as |df| / max(f, 1e-4 ||V^T M W||_F^2)
-because f is a difference of nearly equal terms near the true parameters.
+FP64 path: the GPU solves to rtol 1e-14 (the oracle solves directly) and every
+output must agree to 1e-10 relative (Frobenius norm of the difference over the
+norm of the oracle value).  A residual-based stop at 1e-13 is not enough: the
+measurements weight the far field of each column, where the relative error of a
+solve is larger than its residual suggests (measured: 1.4e-10 in S at rtol 1e-13
+on the 32x32x16 workload, 1.4e-11 at 1e-14).  Mixed precision (FP32 / complex64
+Krylov inside FP64 refinement to rtol 1e-11): 1e-8 relative.  The misfit is
+compared as |df| / max(f, 1e-4 ||V^T M W||_F^2) and the gradient against
+2 ||J|| (||R_s|| + ||S||) (see gpu_setup.grad_err), because both are differences
+of nearly equal terms near the data.
 """
 import numpy as np
 import pytest
@@ -14,9 +19,11 @@ from oracle import dot_oracle as orc
 from paper_1706_05586_gb300 import dot as D
 from paper_1706_05586_gb300 import synth
 from tests import problem
-from tests.gpu_setup import configure, rel
+from tests.gpu_setup import configure, grad_err, rel
 
 pytestmark = pytest.mark.gpu
+
+FP64_RTOL = 1e-14
 
 ROB, DIR = synth.ROBIN, synth.DIRICHLET
 
@@ -87,22 +94,22 @@ def test_pals_absorption(name, ctx):
 @pytest.mark.parametrize("name", list(CASES))
 def test_misfit_gradient_fp64(name, ctx):
     pb, ref = _case(name)
-    configure(ctx, pb, p=pb.inp.p0)
+    configure(ctx, pb, p=pb.inp.p0, rtol=FP64_RTOL)
     f, g, rc = D.dot_gradient(ctx, pb.wl.np_)
     assert rc == D.DOT_OK
     P = pb.inp.V.T @ pb.M @ pb.inp.W
     assert abs(f - ref["f"]) <= 1e-10 * max(ref["f"], 1e-4 * np.sum(np.abs(P) ** 2))
-    assert rel(g, ref["g_p"]) <= 1e-10, (g, ref["g_p"])
+    assert grad_err(g, ref["g_p"], ref["J_p"], ref["R_s"], ref["S"]) <= 1e-10
     S, _ = D.dot_measurements(ctx, pb.wl.ls, pb.wl.ld, _cplx(pb))
     assert rel(S, ref["S"]) <= 1e-10
     st = D.dot_get_stats(ctx)
-    assert st["k"] == pb.wl.ls + pb.wl.ld and st["relres_max"] <= 1e-13
+    assert st["k"] == pb.wl.ls + pb.wl.ld and st["relres_max"] <= FP64_RTOL
 
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_fields_and_jacobians_fp64(name, ctx):
     pb, ref = _case(name)
-    configure(ctx, pb, p=pb.inp.p0)
+    configure(ctx, pb, p=pb.inp.p0, rtol=FP64_RTOL)
     U, Z = D.dot_get_fields(ctx, pb.wl.n, pb.wl.ls, pb.wl.ld, _cplx(pb))
     assert rel(U, ref["Uf"] @ pb.inp.W) <= 1e-10
     assert rel(Z, ref["Zf"] @ pb.inp.V) <= 1e-10
@@ -116,10 +123,10 @@ def test_fields_and_jacobians_fp64(name, ctx):
 def test_gradient_wrt_mua(name, ctx):
     pb, _ = _case(name)
     mu = pb.mu_of(pb.inp.p0)
-    configure(ctx, pb, mua=mu)
+    configure(ctx, pb, mua=mu, rtol=FP64_RTOL)
     f, g, _ = D.dot_gradient(ctx, pb.wl.n)
     ref = orc.evaluate(pb.D, mu, pb.grid, pb.wl.bc, pb.wl.omega_nu, pb.Bd, pb.Cd, pb.M, pb.inp.W, pb.inp.V)
-    assert rel(g, ref["g_mu"]) <= 1e-10
+    assert grad_err(g, ref["g_mu"], ref["J_mu"], ref["R_s"], ref["S"]) <= 1e-10
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -132,20 +139,19 @@ def test_mixed_precision(name, ctx):
     assert st["relres_max"] <= 1e-11 and st["outer_steps"] >= 2
     P = pb.inp.V.T @ pb.M @ pb.inp.W
     assert abs(f - ref["f"]) <= 1e-8 * max(ref["f"], 1e-4 * np.sum(np.abs(P) ** 2))
+    assert grad_err(g, ref["g_p"], ref["J_p"], ref["R_s"], ref["S"]) <= 1e-8
     assert rel(g, ref["g_p"]) <= 1e-8
     S, _ = D.dot_measurements(ctx, pb.wl.ls, pb.wl.ld, _cplx(pb))
     assert rel(S, ref["S"]) <= 1e-8
 
 
 def test_gradient_at_true_parameters(ctx):
-    """Near p_true the misfit is noise-sized; the gradient is checked against the scale
-    2 ||J_p|| ||R_s|| that bounds it."""
+    """Near p_true the residual is noise-sized (1% of S), the case the scaled error is for."""
     pb, _ = _case("dot32x32x16")
     ref = pb.evaluate(pb.inp.p_true)
-    configure(ctx, pb, p=pb.inp.p_true)
+    configure(ctx, pb, p=pb.inp.p_true, rtol=FP64_RTOL)
     f, g, _ = D.dot_gradient(ctx, pb.wl.np_)
-    scale = 2 * np.linalg.norm(ref["J_p"]) * np.linalg.norm(ref["R_s"])
-    assert np.linalg.norm(g - ref["g_p"]) <= 1e-10 * scale
+    assert grad_err(g, ref["g_p"], ref["J_p"], ref["R_s"], ref["S"]) <= 1e-10
     P = pb.inp.V.T @ pb.M @ pb.inp.W
     assert abs(f - ref["f"]) <= 1e-10 * max(ref["f"], 1e-4 * np.sum(np.abs(P) ** 2))
 
@@ -219,3 +225,20 @@ def test_argument_and_state_errors(ctx):
         assert e.value.code == D.DOT_ESTATE
     finally:
         D.dot_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["cplx_11x6x7", "real_13x10x6_l1"])
+def test_forward_model_all_sources(name, ctx):
+    """dot_forward_model returns C^T A^{-1} B for every physical source (Eq. (Eq:compmeas))."""
+    pb, _ = _case(name)
+    mu = pb.mu_of(pb.inp.p0)
+    configure(ctx, pb, mua=mu, rtol=FP64_RTOL)
+    M, rc = D.dot_forward_model(ctx, pb.wl.ns, pb.wl.nd, _cplx(pb))
+    assert rc == D.DOT_OK
+    ref = pb.Cd.T @ orc.solve(pb.A_of(mu), pb.Bd)
+    assert rel(M, ref) <= 1e-10
+    # the sampled state is untouched: the next misfit uses W, V again
+    f, _ = D.dot_misfit(ctx)
+    out = orc.evaluate(pb.D, mu, pb.grid, pb.wl.bc, pb.wl.omega_nu, pb.Bd, pb.Cd, pb.M, pb.inp.W, pb.inp.V)
+    P = pb.inp.V.T @ pb.M @ pb.inp.W
+    assert abs(f - out["f"]) <= 1e-10 * max(out["f"], 1e-4 * np.sum(np.abs(P) ** 2))
