@@ -56,8 +56,9 @@ extern "C" {
 
 /* solver precision */
 #define DOT_PREC_FP64   0  /* FP64 / complex128 Jacobi CG (omega = 0) or COCG     */
-#define DOT_PREC_MIXED  1  /* FP32 / complex64 CG or COCG inside FP64 iterative
-                              refinement; residuals, updates and all outputs FP64 */
+#define DOT_PREC_MIXED  1  /* FP32 / complex64 CG or COCG recurrence with FP64
+                              reliable updates; true residuals, the solution and all
+                              outputs FP64 */
 
 typedef struct dot_ctx dot_ctx;
 
@@ -66,11 +67,11 @@ typedef struct dot_stats {
     int32_t iters_max;       /* max over columns of Krylov iterations (summed over
                                 refinement steps in mixed precision)                   */
     int64_t iters_sum;       /* sum over columns of Krylov iterations                 */
-    int32_t outer_steps;     /* FP64 refinement steps of the last solve (0 for FP64)  */
+    int32_t outer_steps;     /* max over columns of FP64 true-residual refreshes
+                                (reliable updates) of the last solve                  */
     int32_t status;          /* status of the last block solve                        */
-    double  relres_max;      /* max over columns of ||b - A x|| / ||b|| (FP64 true
-                                residual in mixed precision, recurrence residual in
-                                FP64 mode)                                             */
+    double  relres_max;      /* max over columns of the FP64 true residual
+                                ||b - A x|| / ||b|| at the end of the last solve       */
     int64_t columns_solved;  /* cumulative number of PDE solves (columns)             */
     int64_t block_solves;    /* cumulative number of block solves                     */
     double  ms_setup;        /* last: PaLS + coefficients + right-hand sides          */
@@ -144,9 +145,12 @@ int dot_set_sampling(dot_ctx* ctx, int ls, const double* W, int ld, const double
  * (per refinement step in mixed precision; 0 selects 10 (nx + ny + nz)).
  * ls + ld (the block width) may not exceed 1024. */
 int dot_set_solver(dot_ctx* ctx, int precision, double rtol, int maxit);
-/* Mixed precision only: inner relative tolerance of each FP32 solve (default 1e-5)
- * and the maximum number of FP64 refinement steps (default 8). */
-int dot_set_refinement(dot_ctx* ctx, double inner_rtol, int max_outer);
+/* Mixed precision only: reliable-update threshold delta (default 1e-2).  A column's
+ * FP32 recurrence is refreshed from an FP64 true residual b - A x whenever its
+ * recurrence residual falls below delta times its largest value since the last
+ * refresh (and whenever it reaches rtol); convergence is always judged on the FP64
+ * true residual. */
+int dot_set_refinement(dot_ctx* ctx, double delta);
 
 /* Sampled misfit f = ||V^T (C^T A^{-1} B - M) W||_F^2 (Theorem 1 / Eq. (EsTResidual);
  * no factor 1/2; complex: sum of squared real and imaginary parts).  Solves the

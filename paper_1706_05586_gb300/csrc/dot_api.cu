@@ -74,7 +74,7 @@ struct dot_ctx {
     cudaStream_t own = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    int* h_flag = nullptr;  // pinned host word for polling n_active
+    int* h_flag = nullptr;  // pinned host words for polling the column counters
 
     bool grid_set = false;
     int nx = 0, ny = 0, nz = 0;
@@ -107,14 +107,13 @@ struct dot_ctx {
     int prec = DOT_PREC_FP64;
     double rtol = 1e-10;
     int maxit = 0;
-    double inner_rtol = 1e-5;
-    int max_outer = 8;
+    double delta = 1e-2;  // reliable-update threshold of the mixed-precision recurrence
 
-    // block vectors (FP64 and FP32 precisions)
-    DevBuf b64, x64, r64, p64, q64, x32, r32, p32, q32;
-    // per-column state
-    DevBuf cs_rho, cs_alpha, cs_beta, cs_rr, cs_bb, cs_active, cs_iters, cs_status, cs_misc, cs_partA, cs_partB;
-    DevBuf rs_bb, rs_rr, rs_scale, rs_active, rs_misc, rs_partB;
+    // block vectors: FP64 right-hand side, solution and true residual; the recurrence
+    // vectors x~, r~, p, q in the inner precision
+    DevBuf b64, x64, r64, xi, ri, pi, qi;
+    // per-column state (one allocation) and per-block partial sums
+    DevBuf colbuf, partA, partB;
     bool fields_valid = false;
     int fields_status = DOT_OK;
     int kp = 0;
@@ -220,119 +219,156 @@ int ensure_coefficients(dot_ctx* c) {
     return DOT_OK;
 }
 
-int alloc_colstate(dot_ctx* c, int kp, const Launch& L, ColState* st, RefState* rs) {
-    TRY(ensure(c->cs_rho, kp * 16));
-    TRY(ensure(c->cs_alpha, kp * 16));
-    TRY(ensure(c->cs_beta, kp * 16));
-    TRY(ensure(c->cs_rr, kp * 8));
-    TRY(ensure(c->cs_bb, kp * 8));
-    TRY(ensure(c->cs_active, kp * 4));
-    TRY(ensure(c->cs_iters, kp * 4));
-    TRY(ensure(c->cs_status, kp * 4));
-    TRY(ensure(c->cs_misc, 64));
-    TRY(ensure(c->cs_partA, (size_t)L.grid * kp * 16));
-    TRY(ensure(c->cs_partB, (size_t)L.grid * kp * 8));
-    TRY(ensure(c->rs_bb, kp * 8));
-    TRY(ensure(c->rs_rr, kp * 8));
-    TRY(ensure(c->rs_scale, kp * 8));
-    TRY(ensure(c->rs_active, kp * 4));
-    TRY(ensure(c->rs_misc, 64));
-    TRY(ensure(c->rs_partB, (size_t)L.grid * kp * 8));
-    CK(cudaMemsetAsync(c->cs_misc.p, 0, 64, c->s));
-    CK(cudaMemsetAsync(c->rs_misc.p, 0, 64, c->s));
-    CK(cudaMemsetAsync(c->rs_active.p, 0, kp * 4, c->s));
-    st->rho = c->cs_rho.as<double2>();
-    st->alpha = c->cs_alpha.as<double2>();
-    st->beta = c->cs_beta.as<double2>();
-    st->rr = c->cs_rr.as<double>();
-    st->bb = c->cs_bb.as<double>();
-    st->active = c->cs_active.as<int>();
-    st->iters = c->cs_iters.as<int>();
-    st->status = c->cs_status.as<int>();
-    st->n_active = c->cs_misc.as<int>();
-    st->counter = reinterpret_cast<unsigned*>(c->cs_misc.as<int>() + 4);
-    st->partA = c->cs_partA.as<double2>();
-    st->partB = c->cs_partB.as<double>();
-    rs->bb = c->rs_bb.as<double>();
-    rs->rr = c->rs_rr.as<double>();
-    rs->scale = c->rs_scale.as<double>();
-    rs->active = c->rs_active.as<int>();
-    rs->n_active = c->rs_misc.as<int>();
-    rs->counter = reinterpret_cast<unsigned*>(c->rs_misc.as<int>() + 4);
-    rs->partB = c->rs_partB.as<double>();
+int alloc_colstate(dot_ctx* c, int kp, const Launch& L, ColState* st) {
+    const size_t n16 = (size_t)kp * 16, n8 = (size_t)kp * 8, n4 = (size_t)kp * 4;
+    const size_t bytes = 3 * n16 + 7 * n8 + 5 * n4 + 64;
+    TRY(ensure(c->colbuf, bytes));
+    TRY(ensure(c->partA, (size_t)L.grid * kp * 16));
+    TRY(ensure(c->partB, (size_t)L.grid * kp * 8));
+    CK(cudaMemsetAsync(c->colbuf.p, 0, bytes, c->s));
+    char* q = c->colbuf.as<char>();
+    auto take = [&](size_t b) {
+        char* r = q;
+        q += b;
+        return r;
+    };
+    st->rho = reinterpret_cast<double2*>(take(n16));
+    st->alpha = reinterpret_cast<double2*>(take(n16));
+    st->beta = reinterpret_cast<double2*>(take(n16));
+    st->rr = reinterpret_cast<double*>(take(n8));
+    st->maxr = reinterpret_cast<double*>(take(n8));
+    st->scale = reinterpret_cast<double*>(take(n8));
+    st->ratio = reinterpret_cast<double*>(take(n8));
+    st->tol2 = reinterpret_cast<double*>(take(n8));
+    st->bb64 = reinterpret_cast<double*>(take(n8));
+    st->rr64 = reinterpret_cast<double*>(take(n8));
+    st->active = reinterpret_cast<int*>(take(n4));
+    st->upd = reinterpret_cast<int*>(take(n4));
+    st->iters = reinterpret_cast<int*>(take(n4));
+    st->updates = reinterpret_cast<int*>(take(n4));
+    st->status = reinterpret_cast<int*>(take(n4));
+    int* misc = reinterpret_cast<int*>(take(64));
+    st->n_active = misc;
+    st->n_update = misc + 1;
+    st->counter = reinterpret_cast<unsigned*>(misc + 4);
+    st->partA = c->partA.as<double2>();
+    st->partB = c->partB.as<double>();
     return DOT_OK;
 }
 
-int read_flag(dot_ctx* c, const int* dev, int* out) {
-    CK(cudaMemcpyAsync(c->h_flag, dev, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+// Reads n_active and n_update (adjacent words) after the work queued so far.
+int read_counts(dot_ctx* c, const ColState& st, int* act, int* upd) {
+    CK(cudaMemcpyAsync(c->h_flag, st.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
-    *out = *c->h_flag;
+    *act = c->h_flag[0];
+    *upd = c->h_flag[1];
     return DOT_OK;
 }
 
-constexpr int kPoll = 8;  // iterations between host convergence polls
+constexpr int kPoll = 8;  // iterations between host polls
 
-// Iterate until every column of the block has stopped; returns iterations launched.
-int krylov_loop(dot_ctx* c, ElemKind ek, const OpRaw& o, void* x, void* r, void* p, void* q, int kp,
-                const ColState& st, double rtol, int maxit, const Launch& L, int* launched) {
-    int it = 0, act = 0;
-    TRY(read_flag(c, st.n_active, &act));
-    while (act > 0 && it < maxit + kPoll) {
-        for (int m = 0; m < kPoll; ++m)
-            CK(kry_iteration(ek, o, x, r, p, q, c->n, kp, st, rtol, maxit, L, c->s,
-                             c->timing ? &c->tev[4 * m] : nullptr));
-        count(c, 3 * kPoll);
+int collect_step_timing(dot_ctx* c, int steps, bool first_without_p) {
+    for (int m = 0; m < steps; ++m) {
+        float ms = 0.f;
+        if (!(first_without_p && m == 0)) {
+            CK(cudaEventElapsedTime(&ms, c->tev[4 * m], c->tev[4 * m + 1]));
+            c->kt.ms[2] += ms;
+            c->kt.launches[2] += 1;
+        }
+        CK(cudaEventElapsedTime(&ms, c->tev[4 * m + 1], c->tev[4 * m + 2]));
+        c->kt.ms[0] += ms;
+        c->kt.launches[0] += 1;
+        CK(cudaEventElapsedTime(&ms, c->tev[4 * m + 2], c->tev[4 * m + 3]));
+        c->kt.ms[1] += ms;
+        c->kt.launches[1] += 1;
+    }
+    return DOT_OK;
+}
+
+// Block solve of [BW | CV] (already in b64) into x64: Jacobi CG/COCG with the
+// recurrence in `inner` precision and reliable updates in FP64.
+int block_solve(dot_ctx* c, int kp, std::vector<int>& iters, std::vector<int>& updates, std::vector<int>& status,
+                std::vector<double>& rr64, std::vector<double>& bb64) {
+    const int64_t n = c->n;
+    const size_t nk = (size_t)n * kp;
+    const bool mixed = c->prec == DOT_PREC_MIXED;
+    const ElemKind inner = cplx(c) ? (mixed ? EK_C64 : EK_C128) : (mixed ? EK_F32 : EK_F64);
+    const size_t ei = mixed ? esz32(c) : esz64(c);
+    const Launch L = krylov_launch(n, kp, c->num_sms);
+    ColState st;
+    TRY(alloc_colstate(c, kp, L, &st));
+    for (DevBuf* b : {&c->xi, &c->ri, &c->pi, &c->qi}) TRY(ensure(*b, nk * ei));
+    const OpRaw oi = mixed ? op32(c) : op64(c), o64 = op64(c);
+    const double delta = mixed ? c->delta : 0.0;
+    const int maxit = c->maxit > 0 ? c->maxit : 10 * (c->nx + c->ny + c->nz);
+    CK(solve_start(inner, oi, c->b64.p, c->x64.p, c->xi.p, c->ri.p, c->pi.p, n, kp, st, c->rtol, L, c->s));
+    count(c, 2);
+    int act = 0, upd = 0, it = 0;
+    TRY(read_counts(c, st, &act, &upd));
+    bool first = true;
+    while (act > 0 && it < maxit + 2 * kPoll) {
+        const bool first_batch = first;
+        for (int m = 0; m < kPoll; ++m) {
+            CK(kry_step(inner, oi, c->xi.p, c->ri.p, c->pi.p, c->qi.p, n, kp, st, delta, maxit, !first, L, c->s,
+                        c->timing ? &c->tev[4 * m] : nullptr));
+            count(c, first ? 2 : 3);
+            first = false;
+        }
         it += kPoll;
-        TRY(read_flag(c, st.n_active, &act));
-        if (c->timing) {
-            for (int m = 0; m < kPoll; ++m)
-                for (int q3 = 0; q3 < 3; ++q3) {
-                    float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, c->tev[4 * m + q3], c->tev[4 * m + q3 + 1]));
-                    c->kt.ms[q3] += ms;
-                    c->kt.launches[q3] += 1;
-                }
+        TRY(read_counts(c, st, &act, &upd));
+        if (c->timing) TRY(collect_step_timing(c, kPoll, first_batch));
+        if (upd > 0) {
+            if (c->timing) CK(cudaEventRecord(c->tev[32], c->s));
+            CK(solve_refresh(inner, oi, o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, c->ri.p, n, kp, st, c->rtol,
+                             maxit, L, c->num_sms, c->s));
+            count(c, 3);
+            if (c->timing) {
+                CK(cudaEventRecord(c->tev[33], c->s));
+                CK(cudaEventSynchronize(c->tev[33]));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, c->tev[32], c->tev[33]));
+                c->kt.ms[3] += ms;
+                c->kt.launches[3] += 3;
+                c->kt.bytes[3] += (double)upd * n * (6.0 * esz64(c) + 3.0 * ei) + (double)n * 4.0 * 8.0;
+            }
+            TRY(read_counts(c, st, &act, &upd));
         }
     }
-    *launched = it;
-    return DOT_OK;
-}
-
-// Algorithmic bytes of the Krylov kernels of one solve: per column-iteration each
-// vector element is read or written once (stencil: p, q; update: x, p, r, q read and
-// x, r written; direction: r, p read, p written), coefficients once per launch.
-void account_bytes(dot_ctx* c, const std::vector<int>& it_h, size_t es, size_t rs, size_t ds) {
-    if (!c->timing) return;
-    double ci = 0.0;
-    int itmax = 0;
-    for (int v : it_h) {
-        ci += v;
-        itmax = std::max(itmax, v);
-    }
-    const double n = (double)c->n;
-    c->kt.bytes[0] += ci * n * 2.0 * es + itmax * n * 4.0 * rs;
-    c->kt.bytes[1] += ci * n * 6.0 * es + itmax * n * ds;
-    c->kt.bytes[2] += ci * n * 3.0 * es + itmax * n * ds;
-}
-
-// FP64 refinement residual r = b - A x on the columns still refining.
-int timed_ref_residual(dot_ctx* c, ElemKind ek64, const OpRaw& o64, int kp, const RefState& rs, const Launch& L) {
-    int act = kp;
+    iters.resize(kp);
+    updates.resize(kp);
+    status.resize(kp);
+    rr64.resize(kp);
+    bb64.resize(kp);
+    CK(cudaMemcpyAsync(status.data(), st.status, kp * 4, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    bool any_bad = act > 0;
+    for (int j = 0; j < kp; ++j) any_bad = any_bad || status[j] != DOT_OK;
+    CK(solve_finish(inner, o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, n, kp, st, any_bad, L, c->num_sms, c->s));
+    count(c, any_bad ? 2 : 1);
+    CK(cudaMemcpyAsync(iters.data(), st.iters, kp * 4, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(updates.data(), st.updates, kp * 4, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(status.data(), st.status, kp * 4, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(rr64.data(), st.rr64, kp * 8, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(bb64.data(), st.bb64, kp * 8, cudaMemcpyDeviceToHost, c->s));
+    std::vector<int> active(kp);
+    CK(cudaMemcpyAsync(active.data(), st.active, kp * 4, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    for (int j = 0; j < kp; ++j)
+        if (active[j] && status[j] == DOT_OK) status[j] = DOT_ENOTCONV;
     if (c->timing) {
-        TRY(read_flag(c, rs.n_active, &act));
-        CK(cudaEventRecord(c->tev[32], c->s));
-    }
-    CK(ref_residual(ek64, o64, c->b64.p, c->x64.p, c->r64.p, c->n, kp, rs, c->rtol, L, c->s));
-    count(c, 1);
-    if (c->timing) {
-        CK(cudaEventRecord(c->tev[33], c->s));
-        CK(cudaEventSynchronize(c->tev[33]));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, c->tev[32], c->tev[33]));
-        c->kt.ms[3] += ms;
-        c->kt.launches[3] += 1;
-        const double es = esz64(c);
-        c->kt.bytes[3] += (double)act * c->n * 3.0 * es + (double)c->n * 4.0 * 8.0;
+        // algorithmic bytes of the Krylov kernels: every element of a running column read or
+        // written once per launch (stencil: p, q; update: x~, p, r~, q read, x~, r~ written;
+        // direction: r~, p read, p written), coefficients once per launch
+        double ci = 0.0;
+        int itmax = 0;
+        for (int j = 0; j < kp; ++j) {
+            ci += iters[j];
+            itmax = std::max(itmax, iters[j]);
+        }
+        const double nn = (double)n, rs = mixed ? 4.0 : 8.0;
+        c->kt.bytes[0] += ci * nn * 2.0 * ei + itmax * nn * 4.0 * rs;
+        c->kt.bytes[1] += ci * nn * 6.0 * ei + itmax * nn * ei;
+        c->kt.bytes[2] += ci * nn * 3.0 * ei + itmax * nn * ei;
     }
     return DOT_OK;
 }
@@ -347,77 +383,18 @@ int ensure_fields(dot_ctx* c) {
     const int kp = c->ls + c->ld;
     const int64_t n = c->n;
     const size_t nk = (size_t)n * kp;
-    const bool cx_ = cplx(c);
-    const ElemKind ek64 = cx_ ? EK_C128 : EK_F64;
-    const ElemKind ek32 = cx_ ? EK_C64 : EK_F32;
-    const Launch L = krylov_launch(n, kp, c->num_sms);
-    ColState st;
-    RefState rs;
-    TRY(alloc_colstate(c, kp, L, &st, &rs));
     TRY(ensure(c->b64, nk * esz64(c)));
     TRY(ensure(c->x64, nk * esz64(c)));
     TRY(ensure(c->r64, nk * esz64(c)));
     CK(cudaEventRecord(c->ev[0], c->s));
-    CK(build_rhs(cx_, c->rpB.as<int64_t>(), c->ciB.as<int32_t>(), c->vB.as<double>(), c->W.as<double>(), c->ns, c->ls,
-                 c->rpC.as<int64_t>(), c->ciC.as<int32_t>(), c->vC.as<double>(), c->V.as<double>(), c->nd, c->ld, n,
-                 c->b64.p, c->s));
+    CK(build_rhs(cplx(c), c->rpB.as<int64_t>(), c->ciB.as<int32_t>(), c->vB.as<double>(), c->W.as<double>(), c->ns,
+                 c->ls, c->rpC.as<int64_t>(), c->ciC.as<int32_t>(), c->vC.as<double>(), c->V.as<double>(), c->nd,
+                 c->ld, n, c->b64.p, c->s));
     count(c, 1);
     CK(cudaEventRecord(c->ev[1], c->s));
-    const int maxit = c->maxit > 0 ? c->maxit : 10 * (c->nx + c->ny + c->nz);
-    std::vector<int> iters_tot(kp, 0), status(kp, 0), it_h(kp);
-    std::vector<double> rr(kp), bb(kp);
-    int outer = 0;
-    if (c->prec == DOT_PREC_FP64) {
-        TRY(ensure(c->p64, nk * esz64(c)));
-        TRY(ensure(c->q64, nk * esz64(c)));
-        const OpRaw o = op64(c);
-        CK(kry_init(ek64, o, c->b64.p, c->x64.p, c->r64.p, c->p64.p, n, kp, st, L, c->s));
-        int launched = 0;
-        TRY(krylov_loop(c, ek64, o, c->x64.p, c->r64.p, c->p64.p, c->q64.p, kp, st, c->rtol, maxit, L, &launched));
-        CK(cudaMemcpyAsync(it_h.data(), st.iters, kp * 4, cudaMemcpyDeviceToHost, c->s));
-        CK(cudaMemcpyAsync(status.data(), st.status, kp * 4, cudaMemcpyDeviceToHost, c->s));
-        CK(cudaMemcpyAsync(rr.data(), st.rr, kp * 8, cudaMemcpyDeviceToHost, c->s));
-        CK(cudaMemcpyAsync(bb.data(), st.bb, kp * 8, cudaMemcpyDeviceToHost, c->s));
-        CK(cudaStreamSynchronize(c->s));
-        for (int j = 0; j < kp; ++j) iters_tot[j] = it_h[j];
-        account_bytes(c, it_h, esz64(c), 8, esz64(c));
-        count(c, 1);
-    } else {
-        TRY(ensure(c->x32, nk * esz32(c)));
-        TRY(ensure(c->r32, nk * esz32(c)));
-        TRY(ensure(c->p32, nk * esz32(c)));
-        TRY(ensure(c->q32, nk * esz32(c)));
-        const OpRaw o64 = op64(c), o32 = op32(c);
-        CK(ref_init(ek64, c->b64.p, c->x64.p, c->r64.p, n, kp, rs, L, c->s));
-        count(c, 1);
-        int act = 0;
-        for (outer = 0; outer < c->max_outer; ++outer) {
-            if (outer > 0) TRY(timed_ref_residual(c, ek64, o64, kp, rs, L));
-            TRY(read_flag(c, rs.n_active, &act));
-            if (act == 0) break;
-            CK(kry_init_from64(ek32, o32, c->r64.p, rs, c->x32.p, c->r32.p, c->p32.p, n, kp, st, L, c->s));
-            int launched = 0;
-            TRY(krylov_loop(c, ek32, o32, c->x32.p, c->r32.p, c->p32.p, c->q32.p, kp, st, c->inner_rtol, maxit, L,
-                            &launched));
-            CK(ref_promote(ek64, ek32, c->x64.p, c->x32.p, n, kp, rs, L, c->s));
-            CK(cudaMemcpyAsync(it_h.data(), st.iters, kp * 4, cudaMemcpyDeviceToHost, c->s));
-            CK(cudaStreamSynchronize(c->s));
-            for (int j = 0; j < kp; ++j) iters_tot[j] += it_h[j];
-            account_bytes(c, it_h, esz32(c), 4, esz32(c));
-            count(c, 2);
-        }
-        if (outer == c->max_outer) {
-            TRY(timed_ref_residual(c, ek64, o64, kp, rs, L));
-            TRY(read_flag(c, rs.n_active, &act));
-        }
-        CK(cudaMemcpyAsync(rr.data(), rs.rr, kp * 8, cudaMemcpyDeviceToHost, c->s));
-        CK(cudaMemcpyAsync(bb.data(), rs.bb, kp * 8, cudaMemcpyDeviceToHost, c->s));
-        CK(cudaStreamSynchronize(c->s));
-        for (int j = 0; j < kp; ++j) {
-            const bool ok = bb[j] == 0.0 || (std::isfinite(rr[j]) && rr[j] <= c->rtol * c->rtol * bb[j]);
-            status[j] = ok ? DOT_OK : (std::isfinite(rr[j]) ? DOT_ENOTCONV : DOT_EBREAKDOWN);
-        }
-    }
+    std::vector<int> iters, updates, status;
+    std::vector<double> rr, bb;
+    TRY(block_solve(c, kp, iters, updates, status, rr, bb));
     CK(cudaEventRecord(c->ev[2], c->s));
     CK(cudaEventSynchronize(c->ev[2]));
     float ms_rhs = 0, ms_solve = 0;
@@ -425,19 +402,20 @@ int ensure_fields(dot_ctx* c) {
     cudaEventElapsedTime(&ms_solve, c->ev[1], c->ev[2]);
     int st_all = DOT_OK;
     double relmax = 0.0;
-    int itmax = 0;
+    int itmax = 0, updmax = 0;
     int64_t itsum = 0;
     for (int j = 0; j < kp; ++j) {
         if (status[j] == DOT_EBREAKDOWN) st_all = DOT_EBREAKDOWN;
         else if (status[j] == DOT_ENOTCONV && st_all == DOT_OK) st_all = DOT_ENOTCONV;
         if (bb[j] > 0) relmax = std::max(relmax, std::sqrt(rr[j] / bb[j]));
-        itmax = std::max(itmax, iters_tot[j]);
-        itsum += iters_tot[j];
+        itmax = std::max(itmax, iters[j]);
+        updmax = std::max(updmax, updates[j]);
+        itsum += iters[j];
     }
     c->stats.k = kp;
     c->stats.iters_max = itmax;
     c->stats.iters_sum = itsum;
-    c->stats.outer_steps = c->prec == DOT_PREC_FP64 ? 0 : outer;
+    c->stats.outer_steps = updmax;
     c->stats.status = st_all;
     c->stats.relres_max = relmax;
     c->stats.columns_solved += kp;
@@ -554,7 +532,7 @@ int dot_create(dot_ctx** out, int device) {
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_flag, 4 * sizeof(int));
     for (int t = 0; t < 4 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->ev[t]);
     for (int t = 0; t < 34 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->tev[t]);
     if (e != cudaSuccess) {
@@ -573,10 +551,8 @@ int dot_destroy(dot_ctx* c) {
     DevBuf* bufs[] = {&c->D, &c->mu, &c->phi, &c->wdmu, &c->p, &c->cx, &c->cy, &c->cz, &c->dre, &c->dinv64,
                       &c->cx32, &c->cy32, &c->cz32, &c->dre32, &c->dinv32, &c->rpB, &c->ciB, &c->vB, &c->rpC,
                       &c->ciC, &c->vC, &c->cpC, &c->rwC, &c->vCc, &c->W, &c->V, &c->M, &c->MW, &c->P, &c->b64,
-                      &c->x64, &c->r64, &c->p64, &c->q64, &c->x32, &c->r32, &c->p32, &c->q32, &c->cs_rho,
-                      &c->cs_alpha, &c->cs_beta, &c->cs_rr, &c->cs_bb, &c->cs_active, &c->cs_iters, &c->cs_status,
-                      &c->cs_misc, &c->cs_partA, &c->cs_partB, &c->rs_bb, &c->rs_rr, &c->rs_scale, &c->rs_active,
-                      &c->rs_misc, &c->rs_partB, &c->Tm, &c->S, &c->Rs, &c->f, &c->gmu, &c->gp, &c->J, &c->tmp};
+                      &c->x64, &c->r64, &c->xi, &c->ri, &c->pi, &c->qi, &c->colbuf, &c->partA, &c->partB, &c->Tm,
+                      &c->S, &c->Rs, &c->f, &c->gmu, &c->gp, &c->J, &c->tmp};
     for (DevBuf* b : bufs) release(*b);
     for (int t = 0; t < 4; ++t)
         if (c->ev[t]) cudaEventDestroy(c->ev[t]);
@@ -755,12 +731,10 @@ int dot_set_solver(dot_ctx* c, int precision, double rtol, int maxit) {
     return DOT_OK;
 }
 
-int dot_set_refinement(dot_ctx* c, double inner_rtol, int max_outer) {
+int dot_set_refinement(dot_ctx* c, double delta) {
     TRY(need_ctx(c));
-    if (!(inner_rtol > 0.0) || !(inner_rtol < 1.0)) return fail(DOT_EINVAL, "inner_rtol must lie in (0, 1)");
-    if (max_outer < 1) return fail(DOT_EINVAL, "max_outer must be positive");
-    c->inner_rtol = inner_rtol;
-    c->max_outer = max_outer;
+    if (!(delta > 0.0) || !(delta < 1.0)) return fail(DOT_EINVAL, "delta must lie in (0, 1)");
+    c->delta = delta;
     invalidate_fields(c);
     return DOT_OK;
 }

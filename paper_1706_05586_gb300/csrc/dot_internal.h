@@ -8,29 +8,27 @@
 namespace dotk {
 
 // Per-column Krylov state of one block solve (device pointers, length kp unless noted).
+// The recurrence runs on r~ = r / scale; the FP64 solution and true residual are separate.
 struct ColState {
-    double2* rho;      // r^T z (bilinear; imaginary part 0 in real arithmetic)
+    double2* rho;      // r~^T M^{-1} r~ (bilinear; imaginary part 0 in real arithmetic)
     double2* alpha;
     double2* beta;
-    double* rr;        // ||r||_2^2
-    double* bb;        // ||b||_2^2
+    double* rr;        // ||r~||^2 of the recurrence
+    double* maxr;      // max ||r~|| since the last reliable update
+    double* scale;     // s: r~ = r / s
+    double* ratio;     // s_old / s_new of the last refresh
+    double* tol2;      // target for ||r~||^2: rtol^2 ||b||^2 / s^2
+    double* bb64;      // ||b||^2
+    double* rr64;      // ||b - A x||^2 of the FP64 iterate at the last refresh
     int* active;       // 1 while the column iterates
-    int* iters;        // iterations taken
-    int* status;       // 0 ok, DOT_ENOTCONV, DOT_EBREAKDOWN
-    int* n_active;     // [1] number of active columns after the last finaliser
+    int* upd;          // 1 while the column waits for a reliable update
+    int* iters;        // Krylov iterations taken
+    int* updates;      // reliable updates taken
+    int* status;       // DOT_OK, DOT_ENOTCONV, DOT_EBREAKDOWN
+    int* n_active;     // [1] active columns after the last finaliser
+    int* n_update;     // [1] active columns waiting for an update
     unsigned* counter; // [1] arrival counter of the last-block finaliser
     double2* partA;    // [grid * kp] per-block partial sums
-    double* partB;     // [grid * kp]
-};
-
-// Per-column state of the FP64 iterative-refinement loop (mixed precision).
-struct RefState {
-    double* bb;        // ||b||^2 of the FP64 right-hand side
-    double* rr;        // ||b - A x||^2 of the current FP64 iterate
-    double* scale;     // ||r|| used to normalise the FP32 correction problem
-    int* active;       // 1 while the column still needs refinement
-    int* n_active;     // [1]
-    unsigned* counter; // [1]
     double* partB;     // [grid * kp]
 };
 
@@ -55,24 +53,24 @@ struct Launch {
 
 Launch krylov_launch(int64_t n, int kp, int num_sms);
 
-// ---- Krylov (krylov.cu); all enqueue on `s`
-cudaError_t kry_init(ElemKind ek, const OpRaw& op, const void* b, void* x, void* r, void* p,
-                     int64_t n, int kp, const ColState& st, const Launch& L, cudaStream_t s);
-cudaError_t kry_init_from64(ElemKind ek32, const OpRaw& op32, const void* r64, const RefState& rs,
-                            void* x, void* r, void* p, int64_t n, int kp, const ColState& st,
-                            const Launch& L, cudaStream_t s);
-// One Krylov iteration = three launches (stencil + p^T A p, x/r update + convergence,
-// direction update).  ev, when not null, receives four event records around them.
-cudaError_t kry_iteration(ElemKind ek, const OpRaw& op, void* x, void* r, void* p, void* q,
-                          int64_t n, int kp, const ColState& st, double rtol, int maxit,
-                          const Launch& L, cudaStream_t s, cudaEvent_t* ev);
-cudaError_t ref_init(ElemKind ek64, const void* b, void* x, void* r, int64_t n, int kp,
-                     const RefState& rs, const Launch& L, cudaStream_t s);
-cudaError_t ref_residual(ElemKind ek64, const OpRaw& op64, const void* b, const void* x, void* r,
-                         int64_t n, int kp, const RefState& rs, double rtol, const Launch& L,
-                         cudaStream_t s);
-cudaError_t ref_promote(ElemKind ek64, ElemKind ek32, void* x64, const void* x32, int64_t n, int kp,
-                        const RefState& rs, const Launch& L, cudaStream_t s);
+// ---- Krylov (krylov.cu); all enqueue on `s`.  `inner` is the recurrence type
+// (EK_F32/EK_C64 mixed, EK_F64/EK_C128 FP64); the FP64 vectors b64, x64, r64 match it
+// in complexity.
+cudaError_t solve_start(ElemKind inner, const OpRaw& op, const void* b64, void* x64, void* x, void* r, void* p,
+                        int64_t n, int kp, const ColState& st, double rtol, const Launch& L, cudaStream_t s);
+// One Krylov iteration: [direction update,] stencil q = A p with p^T q, then
+// x~/r~ update with convergence / refresh decisions.  ev, when not null, receives
+// four event records around the three launches.
+cudaError_t kry_step(ElemKind inner, const OpRaw& op, void* x, void* r, void* p, void* q, int64_t n, int kp,
+                     const ColState& st, double delta, int maxit, bool with_p, const Launch& L, cudaStream_t s,
+                     cudaEvent_t* ev);
+// Reliable update of the paused columns: promote x~, FP64 true residual, rescale r~.
+cudaError_t solve_refresh(ElemKind inner, const OpRaw& op, const OpRaw& op64, const void* b64, void* x64, void* r64,
+                          void* x, void* r, int64_t n, int kp, const ColState& st, double rtol, int maxit,
+                          const Launch& L, int num_sms, cudaStream_t s);
+// Promote every column's x~; optionally recompute every column's true residual.
+cudaError_t solve_finish(ElemKind inner, const OpRaw& op64, const void* b64, void* x64, void* r64, void* x, int64_t n,
+                         int kp, const ColState& st, bool residual, const Launch& L, int num_sms, cudaStream_t s);
 cudaError_t op_apply(ElemKind ek, const OpRaw& op, const void* x, void* y, int64_t n, int kp,
                      cudaStream_t s);
 

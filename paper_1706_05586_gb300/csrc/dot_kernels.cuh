@@ -104,10 +104,13 @@ struct Op {
 template <typename T>
 __device__ __forceinline__ T apply_at(const Op<T>& op, const T* __restrict__ x, int64_t v, int kp, int c) {
     using R = typename Elem<T>::R;
-    const int64_t nxy = (int64_t)op.nx * op.ny;
-    const int i = (int)(v % op.nx);
-    const int j = (int)((v / op.nx) % op.ny);
-    const int kz = (int)(v / nxy);
+    // grids hold fewer than 2^31 cells, so the index split runs in 32-bit arithmetic
+    const int vi = (int)v;
+    const int nxy = op.nx * op.ny;
+    const int kz = vi / nxy;
+    const int rem = vi - kz * nxy;
+    const int j = rem / op.nx;
+    const int i = rem - j * op.nx;
     const int64_t e = v * kp + c;
     T xc = x[e];
     T acc = escale(op.dre[v], xc);
@@ -116,8 +119,8 @@ __device__ __forceinline__ T apply_at(const Op<T>& op, const T* __restrict__ x, 
     if (i < op.nx - 1)  acc = esub(acc, escale(op.cx[v], x[e + kp]));
     if (j > 0)          acc = esub(acc, escale(op.cy[v - op.nx], x[e - (int64_t)op.nx * kp]));
     if (j < op.ny - 1)  acc = esub(acc, escale(op.cy[v], x[e + (int64_t)op.nx * kp]));
-    if (kz > 0)         acc = esub(acc, escale(op.cz[v - nxy], x[e - nxy * kp]));
-    if (kz < op.nz - 1) acc = esub(acc, escale(op.cz[v], x[e + nxy * kp]));
+    if (kz > 0)         acc = esub(acc, escale(op.cz[v - nxy], x[e - (int64_t)nxy * kp]));
+    if (kz < op.nz - 1) acc = esub(acc, escale(op.cz[v], x[e + (int64_t)nxy * kp]));
     (void)sizeof(R);
     return acc;
 }

@@ -1,4 +1,4 @@
-// Block Jacobi-preconditioned CG / COCG and FP64 iterative refinement (sm_103a).
+// Block Jacobi-preconditioned CG / COCG with reliable updates (sm_103a).
 //
 // k independent Krylov recurrences share one operator A (Sec. 3.3: one block holds
 // the l_s forward columns B W and the l_d adjoint columns C V; A is symmetric, or
@@ -6,10 +6,18 @@
 // applies).  The paper leaves the solver open ("iterative solvers or sparse direct
 // solvers depending on the size"); this is the iterative choice.
 //
+// Precision: the recurrence runs in an inner type (FP32/complex64 in mixed mode,
+// FP64/complex128 otherwise) on a per-column scaled copy r~ = r / s of the residual.
+// The solution lives in FP64.  A column is refreshed ("reliable update",
+// Sleijpen and van der Vorst 1996) when its recurrence residual has dropped below
+// delta times its largest value since the last refresh, or reaches the target: the
+// inner correction is added to the FP64 solution, the true residual b - A x is
+// recomputed in FP64, and the recurrence continues from it with the same search
+// direction.  Convergence is always decided on the FP64 true residual.
+//
 // Reductions are deterministic: each block of a persistent grid writes per-column
 // partial sums, and the last block to arrive sums them in block order and runs the
-// per-column scalar update (alpha, beta, convergence), so no host round trip and
-// no floating-point atomics are needed.
+// per-column scalar update, so no floating-point atomics are used.
 #include "dot_kernels.cuh"
 #include "dot_internal.h"
 #include "dot.h"
@@ -33,7 +41,7 @@ static size_t red_smem(const Launch& L, int kp) {
 
 // -------------------------------------------------------------- block reduction
 // Sum per-column values over the block's voxel slots (fixed order) and store the
-// block's partial sums.  Then report whether this block arrived last.
+// block's partial sums.
 __device__ __forceinline__ void column_partials(double2 a, double b, int kp, int slots, int c, int slot,
                                                 double2* partA, double* partB) {
     extern __shared__ unsigned char smem_raw[];
@@ -55,6 +63,7 @@ __device__ __forceinline__ void column_partials(double2 a, double b, int kp, int
     }
 }
 
+// True in every thread of the last block to finish its partial sums.
 __device__ __forceinline__ bool arrive_last(unsigned* counter) {
     __shared__ int am_last;
     __threadfence();
@@ -83,125 +92,163 @@ __device__ __forceinline__ void sum_partials(const double2* partA, const double*
     *b = rb;
 }
 
-// ------------------------------------------------------------------- kernels
-// x = 0, r = b, p = z = M^{-1} b; rho = b^T z, bb = ||b||^2.
-template <typename T>
-__global__ void k_init(Op<T> op, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
-                       T* __restrict__ p, int64_t n, int kp, int slots, ColState st) {
+// Column counters written by the finalisers: active columns and columns paused for
+// a reliable update.  Also re-arms the arrival counter.
+__device__ __forceinline__ void publish_counts(const ColState& st, int kp) {
+    __shared__ int na, nu;
+    if (threadIdx.x == 0) {
+        na = 0;
+        nu = 0;
+    }
+    __syncthreads();
+    for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
+        if (st.active[cc]) {
+            atomicAdd(&na, 1);
+            if (st.upd[cc]) atomicAdd(&nu, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *st.n_active = na;
+        *st.n_update = nu;
+        *st.counter = 0u;
+    }
+}
+
+#define VOXEL_LOOP(v) \
+    for (int64_t v = (int64_t)blockIdx.x * slots + slot; v < n; v += (int64_t)gridDim.x * slots)
+
+// ------------------------------------------------------------- start of a solve
+// x64 = 0 and ||b||^2 per column; finaliser: scale s = ||b||, activity.
+template <typename T64>
+__global__ void k_start_norm(const T64* __restrict__ b, T64* __restrict__ x64, int64_t n, int kp, int slots,
+                             ColState st, double rtol) {
+    const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
+    double bb = 0.0;
+    VOXEL_LOOP(v) {
+        const int64_t e = v * kp + c;
+        bb += (double)eabs2(b[e]);
+        x64[e] = ezero<T64>();
+    }
+    column_partials(make_double2(0.0, 0.0), bb, kp, slots, c, slot, nullptr, st.partB);
+    if (arrive_last(st.counter)) {
+        for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
+            double2 a;
+            double bsum;
+            sum_partials(nullptr, st.partB, kp, cc, &a, &bsum);
+            const bool fin = isfinite(bsum);
+            st.bb64[cc] = bsum;
+            st.rr64[cc] = bsum;
+            st.scale[cc] = sqrt(bsum);
+            st.tol2[cc] = rtol * rtol;
+            st.iters[cc] = 0;
+            st.upd[cc] = 0;
+            st.updates[cc] = 0;
+            st.status[cc] = fin ? DOT_OK : DOT_EBREAKDOWN;
+            st.active[cc] = fin && bsum > 0.0;
+        }
+        __syncthreads();
+        publish_counts(st, kp);
+    }
+}
+
+// r~ = b / s, x~ = 0, p = M^{-1} r~; rho = r~^T M^{-1} r~, ||r~||^2.
+template <typename T, typename T64>
+__global__ void k_start_inner(Op<T> op, const T64* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
+                              T* __restrict__ p, int64_t n, int kp, int slots, ColState st) {
     using R = typename Elem<T>::R;
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
+    const bool act = st.active[c] != 0;
+    const double inv = act ? 1.0 / st.scale[c] : 0.0;
     T rho = ezero<T>();
-    R bb = 0;
-    for (int64_t v = (int64_t)blockIdx.x * slots + slot; v < n; v += (int64_t)gridDim.x * slots) {
+    R rr = 0;
+    VOXEL_LOOP(v) {
         const int64_t e = v * kp + c;
-        T bv = b[e];
-        T z = emul(op.dinv[v], bv);
         x[e] = ezero<T>();
-        r[e] = bv;
+        if (!act) continue;
+        const T rv = enarrow<T>(ewide(escale(inv, b[e])));
+        const T z = emul(op.dinv[v], rv);
+        r[e] = rv;
         p[e] = z;
-        rho = eadd(rho, emul(bv, z));
-        bb += eabs2(bv);
+        rho = eadd(rho, emul(rv, z));
+        rr += eabs2(rv);
     }
-    column_partials(ewide(rho), (double)bb, kp, slots, c, slot, st.partA, st.partB);
+    column_partials(ewide(rho), (double)rr, kp, slots, c, slot, st.partA, st.partB);
     if (arrive_last(st.counter)) {
-        __shared__ int cnt;
-        if (threadIdx.x == 0) cnt = 0;
-        __syncthreads();
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
+            if (!st.active[cc]) continue;
             double2 a;
-            double bsum;
-            sum_partials(st.partA, st.partB, kp, cc, &a, &bsum);
+            double rsum;
+            sum_partials(st.partA, st.partB, kp, cc, &a, &rsum);
             st.rho[cc] = a;
-            st.bb[cc] = bsum;
-            st.rr[cc] = bsum;
+            st.rr[cc] = rsum;
+            st.maxr[cc] = sqrt(rsum);
             st.beta[cc] = make_double2(0.0, 0.0);
-            st.iters[cc] = 0;
-            const bool fin = isfinite(bsum) && zfinite(a);
-            st.status[cc] = fin ? DOT_OK : DOT_EBREAKDOWN;
-            const int act = fin && bsum > 0.0;
-            st.active[cc] = act;
-            if (act) atomicAdd(&cnt, 1);
+            if (!zfinite(a) || !isfinite(rsum)) {
+                st.status[cc] = DOT_EBREAKDOWN;
+                st.active[cc] = 0;
+            }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            *st.n_active = cnt;
-            *st.counter = 0u;
-        }
+        publish_counts(st, kp);
     }
 }
 
-// Correction problem of one refinement step: b32 = r64 / ||r64|| on the columns
-// still refining (0 elsewhere), then the same start as k_init.
-template <typename T32, typename T64>
-__global__ void k_init_from64(Op<T32> op, const T64* __restrict__ r64, RefState rs, T32* __restrict__ x,
-                              T32* __restrict__ r, T32* __restrict__ p, int64_t n, int kp, int slots,
-                              ColState st) {
-    using R = typename Elem<T32>::R;
-    const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
-    const bool ract = rs.active[c] != 0;
-    const double inv = ract ? 1.0 / rs.scale[c] : 0.0;
-    T32 rho = ezero<T32>();
-    R bb = 0;
-    for (int64_t v = (int64_t)blockIdx.x * slots + slot; v < n; v += (int64_t)gridDim.x * slots) {
-        const int64_t e = v * kp + c;
-        T32 bv = ract ? enarrow<T32>(ewide(escale(inv, r64[e]))) : ezero<T32>();
-        T32 z = emul(op.dinv[v], bv);
-        x[e] = ezero<T32>();
-        r[e] = bv;
-        p[e] = z;
-        rho = eadd(rho, emul(bv, z));
-        bb += eabs2(bv);
-    }
-    column_partials(ewide(rho), (double)bb, kp, slots, c, slot, st.partA, st.partB);
-    if (arrive_last(st.counter)) {
-        __shared__ int cnt;
-        if (threadIdx.x == 0) cnt = 0;
-        __syncthreads();
-        for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-            double2 a;
-            double bsum;
-            sum_partials(st.partA, st.partB, kp, cc, &a, &bsum);
-            st.rho[cc] = a;
-            st.bb[cc] = bsum;
-            st.rr[cc] = bsum;
-            st.beta[cc] = make_double2(0.0, 0.0);
-            st.iters[cc] = 0;
-            const bool fin = isfinite(bsum) && zfinite(a);
-            st.status[cc] = fin ? DOT_OK : DOT_EBREAKDOWN;
-            const int act = fin && bsum > 0.0;
-            st.active[cc] = act;
-            if (act) atomicAdd(&cnt, 1);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            *st.n_active = cnt;
-            *st.counter = 0u;
-        }
-    }
-}
+// -------------------------------------------------------------- one iteration
+__device__ __forceinline__ bool running(const ColState& st, int c) { return st.active[c] && !st.upd[c]; }
 
 // q = A p and pq = p^T q; finaliser alpha = rho / pq.
+// Each thread owns one column of a pencil of voxels (fixed i, j) and marches in z,
+// so the z-neighbours come from registers and the next plane is prefetched; the
+// four in-plane neighbours are coalesced loads served by L1/L2.
 template <typename T>
-__global__ void k_pq(Op<T> op, const T* __restrict__ p, T* __restrict__ q, int64_t n, int kp, int slots,
-                     ColState st) {
+__global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T* __restrict__ q, int kp, int slots,
+                                            ColState st) {
+    using R = typename Elem<T>::R;
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
-    const bool act = st.active[c] != 0;
+    const bool act = running(st, c);
     T pq = ezero<T>();
     if (act) {
-        for (int64_t v = (int64_t)blockIdx.x * slots + slot; v < n; v += (int64_t)gridDim.x * slots) {
-            const int64_t e = v * kp + c;
-            T qv = apply_at(op, p, v, kp, c);
-            q[e] = qv;
-            pq = eadd(pq, emul(p[e], qv));
+        const int nx = op.nx, ny = op.ny, nz = op.nz;
+        const int npen = nx * ny;
+        const int64_t sz = (int64_t)npen * kp;   // one z plane of the block
+        const int64_t sy = (int64_t)nx * kp;
+        for (int pen = blockIdx.x * slots + slot; pen < npen; pen += gridDim.x * slots) {
+            const int i = pen % nx, j = pen / nx;
+            const bool xm = i > 0, xp = i < nx - 1, ym = j > 0, yp = j < ny - 1;
+            int64_t e = (int64_t)pen * kp + c;
+            T pm = ezero<T>();
+            T pc = p[e];
+            T pn = nz > 1 ? p[e + sz] : ezero<T>();
+            R czm = 0;
+            int v = pen;
+#pragma unroll 2
+            for (int k = 0; k < nz; ++k) {
+                const T pnn = (k + 2 < nz) ? p[e + 2 * sz] : ezero<T>();
+                const R czc = (k < nz - 1) ? op.cz[v] : (R)0;
+                T acc = escale(op.dre[v], pc);
+                if (Elem<T>::cplx) acc = eadd(acc, emul_i(op.w, pc));
+                acc = esub(acc, escale(czm, pm));
+                acc = esub(acc, escale(czc, pn));
+                if (xm) acc = esub(acc, escale(op.cx[v - 1], p[e - kp]));
+                if (xp) acc = esub(acc, escale(op.cx[v], p[e + kp]));
+                if (ym) acc = esub(acc, escale(op.cy[v - nx], p[e - sy]));
+                if (yp) acc = esub(acc, escale(op.cy[v], p[e + sy]));
+                q[e] = acc;
+                pq = eadd(pq, emul(pc, acc));
+                pm = pc;
+                pc = pn;
+                pn = pnn;
+                czm = czc;
+                e += sz;
+                v += npen;
+            }
         }
     }
     column_partials(ewide(pq), 0.0, kp, slots, c, slot, st.partA, nullptr);
     if (arrive_last(st.counter)) {
-        __shared__ int cnt;
-        if (threadIdx.x == 0) cnt = 0;
-        __syncthreads();
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-            if (!st.active[cc]) continue;
+            if (!running(st, cc)) continue;
             double2 a;
             double unused;
             sum_partials(st.partA, nullptr, kp, cc, &a, &unused);
@@ -211,46 +258,40 @@ __global__ void k_pq(Op<T> op, const T* __restrict__ p, T* __restrict__ q, int64
                 continue;
             }
             st.alpha[cc] = zdiv(st.rho[cc], a);
-            atomicAdd(&cnt, 1);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            *st.n_active = cnt;
-            *st.counter = 0u;
-        }
+        publish_counts(st, kp);
     }
 }
 
-// x += alpha p, r -= alpha q, rho' = r^T M^{-1} r, ||r||^2; finaliser: convergence
-// test ||r|| <= rtol ||b||, then beta = rho' / rho.
+// x~ += alpha p, r~ -= alpha q, rho' = r~^T M^{-1} r~, ||r~||^2.  Finaliser: pause the
+// column for a reliable update when ||r~|| reached the target or fell below
+// delta * max||r~||; otherwise beta = rho' / rho.
 template <typename T>
 __global__ void k_xr(Op<T> op, const T* __restrict__ p, const T* __restrict__ q, T* __restrict__ x,
-                     T* __restrict__ r, int64_t n, int kp, int slots, ColState st, double rtol, int maxit) {
+                     T* __restrict__ r, int64_t n, int kp, int slots, ColState st, double delta, int maxit) {
     using R = typename Elem<T>::R;
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
-    const bool act = st.active[c] != 0;
+    const bool act = running(st, c);
     T rho = ezero<T>();
     R rr = 0;
     if (act) {
         const T alpha = enarrow<T>(st.alpha[c]);
-        for (int64_t v = (int64_t)blockIdx.x * slots + slot; v < n; v += (int64_t)gridDim.x * slots) {
+        VOXEL_LOOP(v) {
             const int64_t e = v * kp + c;
-            T xv = eadd(x[e], emul(alpha, p[e]));
-            T rv = esub(r[e], emul(alpha, q[e]));
+            const T xv = eadd(x[e], emul(alpha, p[e]));
+            const T rv = esub(r[e], emul(alpha, q[e]));
             x[e] = xv;
             r[e] = rv;
-            T z = emul(op.dinv[v], rv);
+            const T z = emul(op.dinv[v], rv);
             rho = eadd(rho, emul(rv, z));
             rr += eabs2(rv);
         }
     }
     column_partials(ewide(rho), (double)rr, kp, slots, c, slot, st.partA, st.partB);
     if (arrive_last(st.counter)) {
-        __shared__ int cnt;
-        if (threadIdx.x == 0) cnt = 0;
-        __syncthreads();
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-            if (!st.active[cc]) continue;
+            if (!running(st, cc)) continue;
             double2 a;
             double rsum;
             sum_partials(st.partA, st.partB, kp, cc, &a, &rsum);
@@ -262,14 +303,9 @@ __global__ void k_xr(Op<T> op, const T* __restrict__ p, const T* __restrict__ q,
                 st.active[cc] = 0;
                 continue;
             }
-            if (rsum <= rtol * rtol * st.bb[cc]) {
-                st.status[cc] = DOT_OK;
-                st.active[cc] = 0;
-                continue;
-            }
-            if (it >= maxit) {
-                st.status[cc] = DOT_ENOTCONV;
-                st.active[cc] = 0;
+            const double mr = st.maxr[cc];
+            if (rsum <= st.tol2[cc] || rsum < delta * delta * mr * mr || it >= maxit) {
+                st.upd[cc] = 1;  // wait for the FP64 refresh; rho keeps its old value
                 continue;
             }
             const double2 rho_old = st.rho[cc];
@@ -280,119 +316,139 @@ __global__ void k_xr(Op<T> op, const T* __restrict__ p, const T* __restrict__ q,
             }
             st.beta[cc] = zdiv(a, rho_old);
             st.rho[cc] = a;
-            atomicAdd(&cnt, 1);
+            st.maxr[cc] = fmax(mr, sqrt(rsum));
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            *st.n_active = cnt;
-            *st.counter = 0u;
-        }
+        publish_counts(st, kp);
     }
 }
 
-// p = M^{-1} r + beta p
+// p = M^{-1} r~ + beta p
 template <typename T>
 __global__ void k_p(Op<T> op, const T* __restrict__ r, T* __restrict__ p, int64_t n, int kp, int slots,
                     ColState st) {
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
-    if (!st.active[c]) return;
+    if (!running(st, c)) return;
     const T beta = enarrow<T>(st.beta[c]);
-    for (int64_t v = (int64_t)blockIdx.x * slots + slot; v < n; v += (int64_t)gridDim.x * slots) {
+    VOXEL_LOOP(v) {
         const int64_t e = v * kp + c;
         p[e] = eadd(emul(op.dinv[v], r[e]), emul(beta, p[e]));
     }
 }
 
-// ---------------------------------------------------------- FP64 refinement
-template <typename T>
-__global__ void k_ref_init(const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r, int64_t n, int kp,
-                           int slots, RefState rs) {
-    const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
-    double bb = 0.0;
-    for (int64_t v = (int64_t)blockIdx.x * slots + slot; v < n; v += (int64_t)gridDim.x * slots) {
-        const int64_t e = v * kp + c;
-        T bv = b[e];
-        x[e] = ezero<T>();
-        r[e] = bv;
-        bb += (double)eabs2(bv);
-    }
-    column_partials(make_double2(0.0, 0.0), bb, kp, slots, c, slot, nullptr, rs.partB);
-    if (arrive_last(rs.counter)) {
-        __shared__ int cnt;
-        if (threadIdx.x == 0) cnt = 0;
-        __syncthreads();
-        for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-            double2 a;
-            double bsum;
-            sum_partials(nullptr, rs.partB, kp, cc, &a, &bsum);
-            rs.bb[cc] = bsum;
-            rs.rr[cc] = bsum;
-            rs.scale[cc] = sqrt(bsum);
-            const int act = isfinite(bsum) && bsum > 0.0;
-            rs.active[cc] = act;
-            if (act) atomicAdd(&cnt, 1);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            *rs.n_active = cnt;
-            *rs.counter = 0u;
-        }
-    }
-}
-
-// r = b - A x in FP64 on the columns still refining; finaliser: stop a column when
-// ||r|| <= rtol ||b||, else record ||r|| as the next correction's scale.
-template <typename T>
-__global__ void k_ref_resid(Op<T> op, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r,
-                            int64_t n, int kp, int slots, RefState rs, double rtol) {
-    const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
-    const bool act = rs.active[c] != 0;
-    double rr = 0.0;
-    if (act) {
-        for (int64_t v = (int64_t)blockIdx.x * slots + slot; v < n; v += (int64_t)gridDim.x * slots) {
-            const int64_t e = v * kp + c;
-            T rv = esub(b[e], apply_at(op, x, v, kp, c));
-            r[e] = rv;
-            rr += (double)eabs2(rv);
-        }
-    }
-    column_partials(make_double2(0.0, 0.0), rr, kp, slots, c, slot, nullptr, rs.partB);
-    if (arrive_last(rs.counter)) {
-        __shared__ int cnt;
-        if (threadIdx.x == 0) cnt = 0;
-        __syncthreads();
-        for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-            if (!rs.active[cc]) continue;
-            double2 a;
-            double rsum;
-            sum_partials(nullptr, rs.partB, kp, cc, &a, &rsum);
-            rs.rr[cc] = rsum;
-            if (!isfinite(rsum) || rsum <= rtol * rtol * rs.bb[cc]) {
-                rs.active[cc] = 0;
-                continue;
-            }
-            rs.scale[cc] = sqrt(rsum);
-            atomicAdd(&cnt, 1);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            *rs.n_active = cnt;
-            *rs.counter = 0u;
-        }
-    }
-}
-
-template <typename T64, typename T32>
-__global__ void k_ref_promote(T64* __restrict__ x64, const T32* __restrict__ x32, int64_t n, int kp, RefState rs) {
+// ------------------------------------------------------------ reliable update
+// x64 += s x~, x~ = 0 on the paused columns (every column when all != 0).
+template <typename T64, typename T>
+__global__ void k_promote(T64* __restrict__ x64, T* __restrict__ x, int64_t n, int kp, ColState st, int all) {
     const int64_t total = n * kp;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(e % kp);
-        if (!rs.active[c]) continue;
-        const double s = rs.scale[c];
-        double2 d = ewide(x32[e]);
-        T64 add = enarrow<T64>(make_double2(s * d.x, s * d.y));
-        x64[e] = eadd(x64[e], add);
+        if (!(all || (st.active[c] && st.upd[c]))) continue;
+        const double s = st.scale[c];
+        const double2 d = ewide(x[e]);
+        x64[e] = eadd(x64[e], enarrow<T64>(make_double2(s * d.x, s * d.y)));
+        x[e] = ezero<T>();
+    }
+}
+
+// r64 = b - A x64 in FP64 on the paused columns (every column when all != 0).
+// Finaliser (update mode): converged when ||r64|| <= rtol ||b||, stopped when the
+// iteration budget is spent, otherwise the new scale s' = ||r64||, ratio = s / s',
+// and the scaled target tol2 = rtol^2 ||b||^2 / s'^2.
+template <typename T64>
+__global__ void k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64* __restrict__ x64,
+                                T64* __restrict__ r64, int64_t n, int kp, int slots, ColState st, double rtol,
+                                int maxit, int all) {
+    const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
+    const bool sel = all ? true : (st.active[c] && st.upd[c]);
+    double rr = 0.0;
+    if (sel) {
+        VOXEL_LOOP(v) {
+            const int64_t e = v * kp + c;
+            const T64 rv = esub(b[e], apply_at(op, x64, v, kp, c));
+            r64[e] = rv;
+            rr += (double)eabs2(rv);
+        }
+    }
+    column_partials(make_double2(0.0, 0.0), rr, kp, slots, c, slot, nullptr, st.partB);
+    if (arrive_last(st.counter)) {
+        for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
+            const bool s2 = all ? true : (st.active[cc] && st.upd[cc]);
+            if (!s2) continue;
+            double2 a;
+            double rsum;
+            sum_partials(nullptr, st.partB, kp, cc, &a, &rsum);
+            st.rr64[cc] = rsum;
+            if (all) continue;
+            st.updates[cc] += 1;
+            if (!isfinite(rsum)) {
+                st.status[cc] = DOT_EBREAKDOWN;
+                st.active[cc] = 0;
+                st.upd[cc] = 0;
+            } else if (rsum <= rtol * rtol * st.bb64[cc]) {
+                st.status[cc] = DOT_OK;
+                st.active[cc] = 0;
+                st.upd[cc] = 0;
+            } else if (st.iters[cc] >= maxit) {
+                st.status[cc] = DOT_ENOTCONV;
+                st.active[cc] = 0;
+                st.upd[cc] = 0;
+            } else {
+                const double snew = sqrt(rsum);
+                st.ratio[cc] = st.scale[cc] / snew;
+                st.scale[cc] = snew;
+                st.tol2[cc] = rtol * rtol * st.bb64[cc] / rsum;
+            }
+        }
+        __syncthreads();
+        publish_counts(st, kp);
+    }
+}
+
+// r~ = r64 / s' on the refreshed columns; rho' = r~^T M^{-1} r~.  The search
+// direction is kept in the old scale, so beta = (rho' / rho) / ratio carries it over.
+template <typename T, typename T64>
+__global__ void k_refresh(Op<T> op, const T64* __restrict__ r64, T* __restrict__ r, int64_t n, int kp, int slots,
+                          ColState st) {
+    using R = typename Elem<T>::R;
+    const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
+    const bool sel = st.active[c] && st.upd[c];
+    T rho = ezero<T>();
+    R rr = 0;
+    if (sel) {
+        const double inv = 1.0 / st.scale[c];
+        VOXEL_LOOP(v) {
+            const int64_t e = v * kp + c;
+            const T rv = enarrow<T>(ewide(escale(inv, r64[e])));
+            r[e] = rv;
+            rho = eadd(rho, emul(rv, emul(op.dinv[v], rv)));
+            rr += eabs2(rv);
+        }
+    }
+    column_partials(ewide(rho), (double)rr, kp, slots, c, slot, st.partA, st.partB);
+    if (arrive_last(st.counter)) {
+        for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
+            if (!(st.active[cc] && st.upd[cc])) continue;
+            double2 a;
+            double rsum;
+            sum_partials(st.partA, st.partB, kp, cc, &a, &rsum);
+            st.upd[cc] = 0;
+            const double2 rho_old = st.rho[cc];
+            if (!zfinite(a) || !isfinite(rsum) || (rho_old.x == 0.0 && rho_old.y == 0.0)) {
+                st.status[cc] = DOT_EBREAKDOWN;
+                st.active[cc] = 0;
+                continue;
+            }
+            const double2 bq = zdiv(a, rho_old);
+            const double inv_ratio = 1.0 / st.ratio[cc];
+            st.beta[cc] = make_double2(bq.x * inv_ratio, bq.y * inv_ratio);
+            st.rho[cc] = a;
+            st.rr[cc] = rsum;
+            st.maxr[cc] = sqrt(rsum);
+        }
+        __syncthreads();
+        publish_counts(st, kp);
     }
 }
 
@@ -422,102 +478,96 @@ static Op<T> make_op(const OpRaw& o) {
     return op;
 }
 
-#define DOT_DISPATCH(ek, ...)                                         \
-    switch (ek) {                                                     \
-        case EK_F64: { using T = double; __VA_ARGS__; } break;        \
-        case EK_C128: { using T = double2; __VA_ARGS__; } break;      \
-        case EK_F32: { using T = float; __VA_ARGS__; } break;         \
-        case EK_C64: { using T = float2; __VA_ARGS__; } break;        \
-        default: return cudaErrorInvalidValue;                        \
+// (inner, outer) element-type pairs
+#define DOT_DISPATCH2(ek, ...)                                                          \
+    switch (ek) {                                                                       \
+        case EK_F64: { using T = double; using T64 = double; __VA_ARGS__; } break;      \
+        case EK_C128: { using T = double2; using T64 = double2; __VA_ARGS__; } break;   \
+        case EK_F32: { using T = float; using T64 = double; __VA_ARGS__; } break;       \
+        case EK_C64: { using T = float2; using T64 = double2; __VA_ARGS__; } break;     \
+        default: return cudaErrorInvalidValue;                                          \
     }
 
-cudaError_t kry_init(ElemKind ek, const OpRaw& o, const void* b, void* x, void* r, void* p, int64_t n, int kp,
-                     const ColState& st, const Launch& L, cudaStream_t s) {
-    DOT_DISPATCH(ek, (k_init<T><<<L.grid, L.threads, red_smem(L, kp), s>>>(
-                          make_op<T>(o), (const T*)b, (T*)x, (T*)r, (T*)p, n, kp, L.slots, st)));
-    return cudaGetLastError();
+static int grid_elems(int64_t total, int cap) {
+    int64_t b = (total + 255) / 256;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
 }
 
-cudaError_t kry_init_from64(ElemKind ek32, const OpRaw& o, const void* r64, const RefState& rs, void* x,
-                            void* r, void* p, int64_t n, int kp, const ColState& st, const Launch& L,
-                            cudaStream_t s) {
-    if (ek32 == EK_F32)
-        k_init_from64<float, double><<<L.grid, L.threads, red_smem(L, kp), s>>>(
-            make_op<float>(o), (const double*)r64, rs, (float*)x, (float*)r, (float*)p, n, kp, L.slots, st);
-    else if (ek32 == EK_C64)
-        k_init_from64<float2, double2><<<L.grid, L.threads, red_smem(L, kp), s>>>(
-            make_op<float2>(o), (const double2*)r64, rs, (float2*)x, (float2*)r, (float2*)p, n, kp, L.slots, st);
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
-}
-
-cudaError_t kry_iteration(ElemKind ek, const OpRaw& o, void* x, void* r, void* p, void* q, int64_t n, int kp,
-                          const ColState& st, double rtol, int maxit, const Launch& L, cudaStream_t s,
-                          cudaEvent_t* ev) {
-    DOT_DISPATCH(ek, {
-        Op<T> op = make_op<T>(o);
-        if (ev) cudaEventRecord(ev[0], s);
-        k_pq<T><<<L.grid, L.threads, red_smem(L, kp), s>>>(op, (const T*)p, (T*)q, n, kp, L.slots, st);
-        if (ev) cudaEventRecord(ev[1], s);
-        k_xr<T><<<L.grid, L.threads, red_smem(L, kp), s>>>(op, (const T*)p, (const T*)q, (T*)x, (T*)r, n, kp,
-                                                            L.slots, st, rtol, maxit);
-        if (ev) cudaEventRecord(ev[2], s);
-        k_p<T><<<L.grid, L.threads, 0, s>>>(op, (const T*)r, (T*)p, n, kp, L.slots, st);
-        if (ev) cudaEventRecord(ev[3], s);
+cudaError_t solve_start(ElemKind inner, const OpRaw& o, const void* b64, void* x64, void* x, void* r, void* p,
+                        int64_t n, int kp, const ColState& st, double rtol, const Launch& L, cudaStream_t s) {
+    DOT_DISPATCH2(inner, {
+        k_start_norm<T64><<<L.grid, L.threads, red_smem(L, kp), s>>>((const T64*)b64, (T64*)x64, n, kp, L.slots, st,
+                                                                     rtol);
+        k_start_inner<T, T64><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<T>(o), (const T64*)b64, (T*)x,
+                                                                         (T*)r, (T*)p, n, kp, L.slots, st);
     });
     return cudaGetLastError();
 }
 
-cudaError_t ref_init(ElemKind ek64, const void* b, void* x, void* r, int64_t n, int kp, const RefState& rs,
-                     const Launch& L, cudaStream_t s) {
-    if (ek64 == EK_F64)
-        k_ref_init<double><<<L.grid, L.threads, red_smem(L, kp), s>>>((const double*)b, (double*)x, (double*)r, n,
-                                                                      kp, L.slots, rs);
-    else if (ek64 == EK_C128)
-        k_ref_init<double2><<<L.grid, L.threads, red_smem(L, kp), s>>>((const double2*)b, (double2*)x,
-                                                                       (double2*)r, n, kp, L.slots, rs);
-    else
-        return cudaErrorInvalidValue;
+cudaError_t kry_step(ElemKind inner, const OpRaw& o, void* x, void* r, void* p, void* q, int64_t n, int kp,
+                     const ColState& st, double delta, int maxit, bool with_p, const Launch& L, cudaStream_t s,
+                     cudaEvent_t* ev) {
+    DOT_DISPATCH2(inner, {
+        Op<T> op = make_op<T>(o);
+        if (ev) cudaEventRecord(ev[0], s);
+        if (with_p) k_p<T><<<L.grid, L.threads, 0, s>>>(op, (const T*)r, (T*)p, n, kp, L.slots, st);
+        if (ev) cudaEventRecord(ev[1], s);
+        k_pq<T><<<L.grid, L.threads, red_smem(L, kp), s>>>(op, (const T*)p, (T*)q, kp, L.slots, st);
+        if (ev) cudaEventRecord(ev[2], s);
+        k_xr<T><<<L.grid, L.threads, red_smem(L, kp), s>>>(op, (const T*)p, (const T*)q, (T*)x, (T*)r, n, kp,
+                                                            L.slots, st, delta, maxit);
+        if (ev) cudaEventRecord(ev[3], s);
+        (void)sizeof(T64);
+    });
     return cudaGetLastError();
 }
 
-cudaError_t ref_residual(ElemKind ek64, const OpRaw& o, const void* b, const void* x, void* r, int64_t n, int kp,
-                         const RefState& rs, double rtol, const Launch& L, cudaStream_t s) {
-    if (ek64 == EK_F64)
-        k_ref_resid<double><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<double>(o), (const double*)b,
-                                                                       (const double*)x, (double*)r, n, kp,
-                                                                       L.slots, rs, rtol);
-    else if (ek64 == EK_C128)
-        k_ref_resid<double2><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<double2>(o), (const double2*)b,
-                                                                        (const double2*)x, (double2*)r, n, kp,
-                                                                        L.slots, rs, rtol);
-    else
-        return cudaErrorInvalidValue;
+cudaError_t solve_refresh(ElemKind inner, const OpRaw& o, const OpRaw& o64, const void* b64, void* x64, void* r64,
+                          void* x, void* r, int64_t n, int kp, const ColState& st, double rtol, int maxit,
+                          const Launch& L, int num_sms, cudaStream_t s) {
+    const int ge = grid_elems(n * kp, num_sms * 16);
+    DOT_DISPATCH2(inner, {
+        k_promote<T64, T><<<ge, 256, 0, s>>>((T64*)x64, (T*)x, n, kp, st, 0);
+        k_true_residual<T64><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<T64>(o64), (const T64*)b64,
+                                                                        (const T64*)x64, (T64*)r64, n, kp, L.slots,
+                                                                        st, rtol, maxit, 0);
+        k_refresh<T, T64><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<T>(o), (const T64*)r64, (T*)r, n, kp,
+                                                                     L.slots, st);
+    });
     return cudaGetLastError();
 }
 
-cudaError_t ref_promote(ElemKind ek64, ElemKind ek32, void* x64, const void* x32, int64_t n, int kp,
-                        const RefState& rs, const Launch& L, cudaStream_t s) {
-    const int threads = 256;
-    int64_t blocks = (n * kp + threads - 1) / threads;
-    int grid = (int)(blocks < (int64_t)L.grid * 4 ? blocks : (int64_t)L.grid * 4);
-    if (grid < 1) grid = 1;
-    if (ek64 == EK_F64 && ek32 == EK_F32)
-        k_ref_promote<double, float><<<grid, threads, 0, s>>>((double*)x64, (const float*)x32, n, kp, rs);
-    else if (ek64 == EK_C128 && ek32 == EK_C64)
-        k_ref_promote<double2, float2><<<grid, threads, 0, s>>>((double2*)x64, (const float2*)x32, n, kp, rs);
-    else
-        return cudaErrorInvalidValue;
+cudaError_t solve_finish(ElemKind inner, const OpRaw& o64, const void* b64, void* x64, void* r64, void* x, int64_t n,
+                         int kp, const ColState& st, bool residual, const Launch& L, int num_sms, cudaStream_t s) {
+    const int ge = grid_elems(n * kp, num_sms * 16);
+    DOT_DISPATCH2(inner, {
+        k_promote<T64, T><<<ge, 256, 0, s>>>((T64*)x64, (T*)x, n, kp, st, 1);
+        if (residual)
+            k_true_residual<T64><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<T64>(o64), (const T64*)b64,
+                                                                            (const T64*)x64, (T64*)r64, n, kp,
+                                                                            L.slots, st, 0.0, 0, 1);
+    });
     return cudaGetLastError();
 }
 
 cudaError_t op_apply(ElemKind ek, const OpRaw& o, const void* x, void* y, int64_t n, int kp, cudaStream_t s) {
-    const int threads = 256;
-    int64_t blocks = (n * kp + threads - 1) / threads;
-    int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
-    if (grid < 1) grid = 1;
-    DOT_DISPATCH(ek, (k_apply<T><<<grid, threads, 0, s>>>(make_op<T>(o), (const T*)x, (T*)y, n, kp)));
+    const int grid = grid_elems(n * kp, 152 * 16);
+    switch (ek) {
+        case EK_F64:
+            k_apply<double><<<grid, 256, 0, s>>>(make_op<double>(o), (const double*)x, (double*)y, n, kp);
+            break;
+        case EK_C128:
+            k_apply<double2><<<grid, 256, 0, s>>>(make_op<double2>(o), (const double2*)x, (double2*)y, n, kp);
+            break;
+        case EK_F32:
+            k_apply<float><<<grid, 256, 0, s>>>(make_op<float>(o), (const float*)x, (float*)y, n, kp);
+            break;
+        case EK_C64:
+            k_apply<float2><<<grid, 256, 0, s>>>(make_op<float2>(o), (const float2*)x, (float2*)y, n, kp);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

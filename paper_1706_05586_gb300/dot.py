@@ -45,7 +45,7 @@ SIGNATURES = {
     "dot_set_data": [C.c_void_p, C.c_void_p, C.c_int],
     "dot_set_sampling": [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p],
     "dot_set_solver": [C.c_void_p, C.c_int, C.c_double, C.c_int],
-    "dot_set_refinement": [C.c_void_p, C.c_double, C.c_int],
+    "dot_set_refinement": [C.c_void_p, C.c_double],
     "dot_misfit": [C.c_void_p, C.c_void_p],
     "dot_measurements": [C.c_void_p, C.c_void_p],
     "dot_forward_model": [C.c_void_p, C.c_void_p],
@@ -207,8 +207,8 @@ def dot_set_solver(ctx, precision, rtol, maxit=0):
     return _check(load().dot_set_solver(ctx, int(precision), float(rtol), int(maxit)))
 
 
-def dot_set_refinement(ctx, inner_rtol, max_outer):
-    return _check(load().dot_set_refinement(ctx, float(inner_rtol), int(max_outer)))
+def dot_set_refinement(ctx, delta):
+    return _check(load().dot_set_refinement(ctx, float(delta)))
 
 
 def dot_misfit(ctx, allow=()):

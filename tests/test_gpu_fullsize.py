@@ -67,7 +67,7 @@ def test_true_residual_every_column(setup):
 def test_one_column_against_oracle_solve(setup):
     h, inp, A = setup["h"], setup["inp"], setup["A"]
     b0 = setup["B"] @ inp.W[:, 0]
-    u0, _ = orc.krylov_solve(A, b0.astype(complex), rtol=1e-12)
+    u0, _ = orc.krylov_solve(A, b0.astype(complex), rtol=1e-14)
     U, _ = D.dot_get_fields(h, WL.n, WL.ls, WL.ld, True)
     assert np.linalg.norm(U[:, 0] - u0) <= 1e-8 * np.linalg.norm(u0)
     S, _ = D.dot_measurements(h, WL.ls, WL.ld, True)
