@@ -279,19 +279,27 @@ def run_ours(args):
                       "parallelism": f"replicas x{ws}"},
            "clocks": clk, "gpu_launches": int(launches), "roofline": roofline}
 
-    # plain FP64 GPU path at the last p: accuracy of the mixed path and its own throughput
+    # plain FP64 GPU path at the last p: its throughput at the same stopping rule, and a
+    # tight FP64 reference (rtol 1e-13) for the error of each output
     if not args.no_fp64_compare and args.precision == "mixed":
-        D.dot_set_solver(ctx, D.PREC_FP64, args.rtol, 0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        f64, g64, _ = D.dot_gradient(ctx, wl.np_)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        out["fp64_path"] = {"evals_per_s": round(1e3 / ms64, 4), "ms_per_eval": round(ms64, 1),
-                            "iters": D.dot_get_stats(ctx)["iters_max"]}
-        out["err_vs_fp64"] = {"f": abs(f_last - f64) / abs(f64),
-                              "g": float(np.linalg.norm(g_last - g64) / np.linalg.norm(g64))}
+        def fp64_eval(rtol):
+            D.dot_set_solver(ctx, D.PREC_FP64, rtol, 0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f64, g64, _ = D.dot_gradient(ctx, wl.np_)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            S64, _ = D.dot_measurements(ctx, wl.ls, wl.ld, wl.omega_nu != 0.0)
+            return f64, g64, S64, e0.elapsed_time(e1), D.dot_get_stats(ctx)
+        S_last, _ = D.dot_measurements(ctx, wl.ls, wl.ld, wl.omega_nu != 0.0)
+        fa, ga, Sa, ms64, st64 = fp64_eval(args.rtol)
+        fr, gr, Sr, msr, str_ = fp64_eval(1e-13)
+        rel = lambda a, b: float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+        out["fp64_path"] = {"evals_per_s": round(1e3 / ms64, 4), "ms_per_eval": round(ms64, 1), "rtol": args.rtol,
+                            "iters": st64["iters_max"], "speedup_of_mixed": round(ms64 / (ms_max / args.steps), 3)}
+        out["err_vs_fp64"] = {"reference": "plain FP64 GPU path at rtol 1e-13 (%d iterations)" % str_["iters_max"],
+                              "mixed": {"f": abs(f_last - fr) / abs(fr), "g": rel(g_last, gr), "S": rel(S_last, Sr)},
+                              "fp64_same_rtol": {"f": abs(fa - fr) / abs(fr), "g": rel(ga, gr), "S": rel(Sa, Sr)}}
         D.dot_set_solver(ctx, D.PREC_MIXED, args.rtol, 0)
 
     # end to end through the C ABI with host buffers (all inputs copied every step)

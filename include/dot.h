@@ -145,11 +145,11 @@ int dot_set_sampling(dot_ctx* ctx, int ls, const double* W, int ld, const double
  * (per refinement step in mixed precision; 0 selects 10 (nx + ny + nz)).
  * ls + ld (the block width) may not exceed 1024. */
 int dot_set_solver(dot_ctx* ctx, int precision, double rtol, int maxit);
-/* Mixed precision only: reliable-update threshold delta (default 1e-2).  A column's
+/* Mixed precision only: reliable-update threshold delta (default 1e-3).  A column's
  * FP32 recurrence is refreshed from an FP64 true residual b - A x whenever its
  * recurrence residual falls below delta times its largest value since the last
- * refresh (and whenever it reaches rtol); convergence is always judged on the FP64
- * true residual. */
+ * refresh, after 256 iterations without a refresh, and whenever it reaches rtol;
+ * convergence is always judged on the FP64 true residual. */
 int dot_set_refinement(dot_ctx* ctx, double delta);
 
 /* Sampled misfit f = ||V^T (C^T A^{-1} B - M) W||_F^2 (Theorem 1 / Eq. (EsTResidual);

@@ -107,7 +107,7 @@ struct dot_ctx {
     int prec = DOT_PREC_FP64;
     double rtol = 1e-10;
     int maxit = 0;
-    double delta = 1e-2;  // reliable-update threshold of the mixed-precision recurrence
+    double delta = 1e-3;  // reliable-update threshold of the mixed-precision recurrence
 
     // block vectors: FP64 right-hand side, solution and true residual; the recurrence
     // vectors x~, r~, p, q in the inner precision
@@ -221,7 +221,7 @@ int ensure_coefficients(dot_ctx* c) {
 
 int alloc_colstate(dot_ctx* c, int kp, const Launch& L, ColState* st) {
     const size_t n16 = (size_t)kp * 16, n8 = (size_t)kp * 8, n4 = (size_t)kp * 4;
-    const size_t bytes = 3 * n16 + 7 * n8 + 5 * n4 + 64;
+    const size_t bytes = 3 * n16 + 7 * n8 + 6 * n4 + 64;
     TRY(ensure(c->colbuf, bytes));
     TRY(ensure(c->partA, (size_t)L.grid * kp * 16));
     TRY(ensure(c->partB, (size_t)L.grid * kp * 8));
@@ -246,6 +246,7 @@ int alloc_colstate(dot_ctx* c, int kp, const Launch& L, ColState* st) {
     st->upd = reinterpret_cast<int*>(take(n4));
     st->iters = reinterpret_cast<int*>(take(n4));
     st->updates = reinterpret_cast<int*>(take(n4));
+    st->since = reinterpret_cast<int*>(take(n4));
     st->status = reinterpret_cast<int*>(take(n4));
     int* misc = reinterpret_cast<int*>(take(64));
     st->n_active = misc;

@@ -24,6 +24,7 @@ struct ColState {
     int* upd;          // 1 while the column waits for a reliable update
     int* iters;        // Krylov iterations taken
     int* updates;      // reliable updates taken
+    int* since;        // iterations since the last refresh
     int* status;       // DOT_OK, DOT_ENOTCONV, DOT_EBREAKDOWN
     int* n_active;     // [1] active columns after the last finaliser
     int* n_update;     // [1] active columns waiting for an update

@@ -115,6 +115,8 @@ __device__ __forceinline__ void publish_counts(const ColState& st, int kp) {
     }
 }
 
+constexpr int kRefreshEvery = 256;
+
 #define VOXEL_LOOP(v) \
     for (int64_t v = (int64_t)blockIdx.x * slots + slot; v < n; v += (int64_t)gridDim.x * slots)
 
@@ -144,6 +146,7 @@ __global__ void k_start_norm(const T64* __restrict__ b, T64* __restrict__ x64, i
             st.iters[cc] = 0;
             st.upd[cc] = 0;
             st.updates[cc] = 0;
+            st.since[cc] = 0;
             st.status[cc] = fin ? DOT_OK : DOT_EBREAKDOWN;
             st.active[cc] = fin && bsum > 0.0;
         }
@@ -304,7 +307,13 @@ __global__ void k_xr(Op<T> op, const T* __restrict__ p, const T* __restrict__ q,
                 continue;
             }
             const double mr = st.maxr[cc];
-            if (rsum <= st.tol2[cc] || rsum < delta * delta * mr * mr || it >= maxit) {
+            const int since = st.since[cc] + 1;
+            st.since[cc] = since;
+            // refresh at the target, after a drop by delta, at the iteration budget, and (in
+            // mixed precision) at least every kRefreshEvery iterations so that a recurrence
+            // that drifted from the true residual cannot stall the column
+            if (rsum <= st.tol2[cc] || rsum < delta * delta * mr * mr || it >= maxit ||
+                (delta > 0.0 && since >= kRefreshEvery)) {
                 st.upd[cc] = 1;  // wait for the FP64 refresh; rho keeps its old value
                 continue;
             }
@@ -446,6 +455,7 @@ __global__ void k_refresh(Op<T> op, const T64* __restrict__ r64, T* __restrict__
             st.rho[cc] = a;
             st.rr[cc] = rsum;
             st.maxr[cc] = sqrt(rsum);
+            st.since[cc] = 0;
         }
         __syncthreads();
         publish_counts(st, kp);

@@ -7,7 +7,7 @@ norm of the oracle value).  A residual-based stop at 1e-13 is not enough: the
 measurements weight the far field of each column, where the relative error of a
 solve is larger than its residual suggests (measured: 1.4e-10 in S at rtol 1e-13
 on the 32x32x16 workload, 1.4e-11 at 1e-14).  Mixed precision (FP32 / complex64
-Krylov inside FP64 refinement to rtol 1e-11): 1e-8 relative.  The misfit is
+recurrence with FP64 reliable updates, true residual to 1e-13): 1e-8 relative.  The misfit is
 compared as |df| / max(f, 1e-4 ||V^T M W||_F^2) and the gradient against
 2 ||J|| (||R_s|| + ||S||) (see gpu_setup.grad_err), because both are differences
 of nearly equal terms near the data.
@@ -132,11 +132,11 @@ def test_gradient_wrt_mua(name, ctx):
 @pytest.mark.parametrize("name", list(CASES))
 def test_mixed_precision(name, ctx):
     pb, ref = _case(name)
-    configure(ctx, pb, p=pb.inp.p0, prec=D.PREC_MIXED, rtol=1e-11)
+    configure(ctx, pb, p=pb.inp.p0, prec=D.PREC_MIXED, rtol=1e-13)
     f, g, rc = D.dot_gradient(ctx, pb.wl.np_)
     assert rc == D.DOT_OK
     st = D.dot_get_stats(ctx)
-    assert st["relres_max"] <= 1e-11 and st["outer_steps"] >= 2
+    assert st["relres_max"] <= 1e-13 and st["outer_steps"] >= 2
     P = pb.inp.V.T @ pb.M @ pb.inp.W
     assert abs(f - ref["f"]) <= 1e-8 * max(ref["f"], 1e-4 * np.sum(np.abs(P) ** 2))
     assert grad_err(g, ref["g_p"], ref["J_p"], ref["R_s"], ref["S"]) <= 1e-8
