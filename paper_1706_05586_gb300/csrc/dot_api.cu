@@ -219,12 +219,12 @@ int ensure_coefficients(dot_ctx* c) {
     return DOT_OK;
 }
 
-int alloc_colstate(dot_ctx* c, int kp, const Launch& L, ColState* st) {
+int alloc_colstate(dot_ctx* c, int kp, int max_grid, ColState* st) {
     const size_t n16 = (size_t)kp * 16, n8 = (size_t)kp * 8, n4 = (size_t)kp * 4;
     const size_t bytes = 3 * n16 + 7 * n8 + 6 * n4 + 64;
     TRY(ensure(c->colbuf, bytes));
-    TRY(ensure(c->partA, (size_t)L.grid * kp * 16));
-    TRY(ensure(c->partB, (size_t)L.grid * kp * 8));
+    TRY(ensure(c->partA, (size_t)max_grid * kp * 16));
+    TRY(ensure(c->partB, (size_t)max_grid * kp * 8));
     CK(cudaMemsetAsync(c->colbuf.p, 0, bytes, c->s));
     char* q = c->colbuf.as<char>();
     auto take = [&](size_t b) {
@@ -288,6 +288,7 @@ int collect_step_timing(dot_ctx* c, int steps, bool first_without_p) {
 
 // Block solve of [BW | CV] (already in b64) into x64: Jacobi CG/COCG with the
 // recurrence in `inner` precision and reliable updates in FP64.
+// kp is the padded block width (a multiple of 4); padded columns have b = 0 and stay idle.
 int block_solve(dot_ctx* c, int kp, std::vector<int>& iters, std::vector<int>& updates, std::vector<int>& status,
                 std::vector<double>& rr64, std::vector<double>& bb64) {
     const int64_t n = c->n;
@@ -296,8 +297,9 @@ int block_solve(dot_ctx* c, int kp, std::vector<int>& iters, std::vector<int>& u
     const ElemKind inner = cplx(c) ? (mixed ? EK_C64 : EK_C128) : (mixed ? EK_F32 : EK_F64);
     const size_t ei = mixed ? esz32(c) : esz64(c);
     const Launch L = krylov_launch(n, kp, c->num_sms);
+    const Launch Lv = vector_launch(n, kp, vector_width(inner), c->num_sms);
     ColState st;
-    TRY(alloc_colstate(c, kp, L, &st));
+    TRY(alloc_colstate(c, kp, std::max(L.grid, Lv.grid), &st));
     for (DevBuf* b : {&c->xi, &c->ri, &c->pi, &c->qi}) TRY(ensure(*b, nk * ei));
     const OpRaw oi = mixed ? op32(c) : op64(c), o64 = op64(c);
     const double delta = mixed ? c->delta : 0.0;
@@ -310,7 +312,7 @@ int block_solve(dot_ctx* c, int kp, std::vector<int>& iters, std::vector<int>& u
     while (act > 0 && it < maxit + 2 * kPoll) {
         const bool first_batch = first;
         for (int m = 0; m < kPoll; ++m) {
-            CK(kry_step(inner, oi, c->xi.p, c->ri.p, c->pi.p, c->qi.p, n, kp, st, delta, maxit, !first, L, c->s,
+            CK(kry_step(inner, oi, c->xi.p, c->ri.p, c->pi.p, c->qi.p, n, kp, st, delta, maxit, !first, Lv, c->s,
                         c->timing ? &c->tev[4 * m] : nullptr));
             count(c, first ? 2 : 3);
             first = false;
@@ -381,7 +383,8 @@ int ensure_fields(dot_ctx* c) {
     if (c->nd == 0) return fail(DOT_ESTATE, "dot_set_detectors has not been called");
     if (c->ls == 0 && c->ld == 0) return fail(DOT_ESTATE, "dot_set_sampling has not been called");
     TRY(kp_limit_check(c));
-    const int kp = c->ls + c->ld;
+    const int kr = c->ls + c->ld;       // columns of the block
+    const int kp = (kr + 3) & ~3;       // padded stride: 16-byte vector access in every precision
     const int64_t n = c->n;
     const size_t nk = (size_t)n * kp;
     TRY(ensure(c->b64, nk * esz64(c)));
@@ -390,7 +393,7 @@ int ensure_fields(dot_ctx* c) {
     CK(cudaEventRecord(c->ev[0], c->s));
     CK(build_rhs(cplx(c), c->rpB.as<int64_t>(), c->ciB.as<int32_t>(), c->vB.as<double>(), c->W.as<double>(), c->ns,
                  c->ls, c->rpC.as<int64_t>(), c->ciC.as<int32_t>(), c->vC.as<double>(), c->V.as<double>(), c->nd,
-                 c->ld, n, c->b64.p, c->s));
+                 c->ld, n, kp, c->b64.p, c->s));
     count(c, 1);
     CK(cudaEventRecord(c->ev[1], c->s));
     std::vector<int> iters, updates, status;
@@ -405,7 +408,7 @@ int ensure_fields(dot_ctx* c) {
     double relmax = 0.0;
     int itmax = 0, updmax = 0;
     int64_t itsum = 0;
-    for (int j = 0; j < kp; ++j) {
+    for (int j = 0; j < kr; ++j) {
         if (status[j] == DOT_EBREAKDOWN) st_all = DOT_EBREAKDOWN;
         else if (status[j] == DOT_ENOTCONV && st_all == DOT_OK) st_all = DOT_ENOTCONV;
         if (bb[j] > 0) relmax = std::max(relmax, std::sqrt(rr[j] / bb[j]));
@@ -413,13 +416,13 @@ int ensure_fields(dot_ctx* c) {
         updmax = std::max(updmax, updates[j]);
         itsum += iters[j];
     }
-    c->stats.k = kp;
+    c->stats.k = kr;
     c->stats.iters_max = itmax;
     c->stats.iters_sum = itsum;
     c->stats.outer_steps = updmax;
     c->stats.status = st_all;
     c->stats.relres_max = relmax;
-    c->stats.columns_solved += kp;
+    c->stats.columns_solved += kr;
     c->stats.block_solves += 1;
     c->stats.ms_setup = ms_rhs;
     c->stats.ms_solve = ms_solve;

@@ -52,7 +52,12 @@ struct Launch {
     int threads;   // kp * slots
 };
 
+// Launch shape of the scalar kernels (one column per thread, four blocks per SM).
 Launch krylov_launch(int64_t n, int kp, int num_sms);
+// Launch shape of the vectorised iteration kernels (W columns per thread).
+Launch vector_launch(int64_t n, int kp, int w, int num_sms);
+// Columns per thread of the iteration kernels for a recurrence type (kp is padded to 4).
+int vector_width(ElemKind inner);
 
 // ---- Krylov (krylov.cu); all enqueue on `s`.  `inner` is the recurrence type
 // (EK_F32/EK_C64 mixed, EK_F64/EK_C128 FP64); the FP64 vectors b64, x64, r64 match it
@@ -63,7 +68,7 @@ cudaError_t solve_start(ElemKind inner, const OpRaw& op, const void* b64, void* 
 // x~/r~ update with convergence / refresh decisions.  ev, when not null, receives
 // four event records around the three launches.
 cudaError_t kry_step(ElemKind inner, const OpRaw& op, void* x, void* r, void* p, void* q, int64_t n, int kp,
-                     const ColState& st, double delta, int maxit, bool with_p, const Launch& L, cudaStream_t s,
+                     const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv, cudaStream_t s,
                      cudaEvent_t* ev);
 // Reliable update of the paused columns: promote x~, FP64 true residual, rescale r~.
 cudaError_t solve_refresh(ElemKind inner, const OpRaw& op, const OpRaw& op64, const void* b64, void* x64, void* r64,
@@ -85,7 +90,7 @@ cudaError_t build_coefficients(const double* D, const double* mu, int nx, int ny
                                float* cz32, float* dre32, void* dinv32, cudaStream_t s);
 cudaError_t build_rhs(bool cplx, const int64_t* rowptrB, const int32_t* colB, const double* valB,
                       const double* W, int ns, int ls, const int64_t* rowptrC, const int32_t* colC,
-                      const double* valC, const double* V, int nd, int ld, int64_t n, void* X,
+                      const double* valC, const double* V, int nd, int ld, int64_t n, int kp, void* X,
                       cudaStream_t s);
 cudaError_t blk_from_colmajor(bool cplx, const double* cm, int64_t n, int k, int kp, int c0,
                               void* blk, cudaStream_t s);

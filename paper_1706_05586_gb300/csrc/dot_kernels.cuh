@@ -83,6 +83,35 @@ __device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
 }
 __device__ __forceinline__ bool zfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 
+// ------------------------------------------------------- 16-byte vector access
+// A thread of the Krylov kernels owns W = 16 / sizeof(T) consecutive columns of a
+// voxel and moves them with one 16-byte load or store (block widths are padded to a
+// multiple of 4 columns, so every such access is 16-byte aligned).
+template <typename T> struct Vec16;
+template <> struct Vec16<float>   { static constexpr int W = 4; using L = float4; };
+template <> struct Vec16<float2>  { static constexpr int W = 2; using L = float4; };
+template <> struct Vec16<double>  { static constexpr int W = 2; using L = double2; };
+template <> struct Vec16<double2> { static constexpr int W = 1; using L = double2; };
+
+template <typename T>
+struct alignas(16) V16 {
+    T e[Vec16<T>::W];
+};
+
+template <typename T>
+__device__ __forceinline__ V16<T> ld16(const T* __restrict__ p) {
+    typename Vec16<T>::L t = *reinterpret_cast<const typename Vec16<T>::L*>(p);
+    V16<T> r;
+    memcpy(&r, &t, 16);
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ void st16(T* __restrict__ p, const V16<T>& v) {
+    typename Vec16<T>::L t;
+    memcpy(&t, &v, 16);
+    *reinterpret_cast<typename Vec16<T>::L*>(p) = t;
+}
+
 // ---------------------------------------------------------------- operator
 // Coefficients of (A(mu) + i w I), per unit volume:
 //   (A u)_v = dre_v u_v + i w u_v - sum_faces cf * u_nb

@@ -155,8 +155,8 @@ template <typename T>
 __global__ void k_rhs(const int64_t* __restrict__ rpB, const int32_t* __restrict__ ciB, const double* __restrict__ vB,
                       const double* __restrict__ W, int ns, int ls, const int64_t* __restrict__ rpC,
                       const int32_t* __restrict__ ciC, const double* __restrict__ vC, const double* __restrict__ V,
-                      int nd, int ld, int64_t n, T* __restrict__ X) {
-    const int kp = ls + ld;
+                      int nd, int ld, int64_t n, int kp, T* __restrict__ X) {
+    // columns ls + ld .. kp - 1 pad the block to a multiple of 4 and stay zero
     const int64_t total = n * kp;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = e / kp;
@@ -164,7 +164,7 @@ __global__ void k_rhs(const int64_t* __restrict__ rpB, const int32_t* __restrict
         double acc = 0.0;
         if (c < ls) {
             for (int64_t t = rpB[v]; t < rpB[v + 1]; ++t) acc += vB[t] * W[ciB[t] + (int64_t)ns * c];
-        } else {
+        } else if (c < ls + ld) {
             const int l = c - ls;
             for (int64_t t = rpC[v]; t < rpC[v + 1]; ++t) acc += vC[t] * V[ciC[t] + (int64_t)nd * l];
         }
@@ -174,12 +174,12 @@ __global__ void k_rhs(const int64_t* __restrict__ rpB, const int32_t* __restrict
 
 cudaError_t build_rhs(bool cplx, const int64_t* rpB, const int32_t* ciB, const double* vB, const double* W, int ns,
                       int ls, const int64_t* rpC, const int32_t* ciC, const double* vC, const double* V, int nd,
-                      int ld, int64_t n, void* X, cudaStream_t s) {
-    const int g = grid_for(n * (ls + ld), 256);
+                      int ld, int64_t n, int kp, void* X, cudaStream_t s) {
+    const int g = grid_for(n * kp, 256);
     if (cplx)
-        k_rhs<double2><<<g, 256, 0, s>>>(rpB, ciB, vB, W, ns, ls, rpC, ciC, vC, V, nd, ld, n, (double2*)X);
+        k_rhs<double2><<<g, 256, 0, s>>>(rpB, ciB, vB, W, ns, ls, rpC, ciC, vC, V, nd, ld, n, kp, (double2*)X);
     else
-        k_rhs<double><<<g, 256, 0, s>>>(rpB, ciB, vB, W, ns, ls, rpC, ciC, vC, V, nd, ld, n, (double*)X);
+        k_rhs<double><<<g, 256, 0, s>>>(rpB, ciB, vB, W, ns, ls, rpC, ciC, vC, V, nd, ld, n, kp, (double*)X);
     return cudaGetLastError();
 }
 

@@ -200,55 +200,109 @@ __global__ void k_start_inner(Op<T> op, const T64* __restrict__ b, T* __restrict
 // -------------------------------------------------------------- one iteration
 __device__ __forceinline__ bool running(const ColState& st, int c) { return st.active[c] && !st.upd[c]; }
 
-// q = A p and pq = p^T q; finaliser alpha = rho / pq.
-// Each thread owns one column of a pencil of voxels (fixed i, j) and marches in z,
-// so the z-neighbours come from registers and the next plane is prefetched; the
-// four in-plane neighbours are coalesced loads served by L1/L2.
+// Launch shape of the vectorised iteration kernels: kp / W threads per voxel, about
+// 256 threads per block, eight blocks per SM.
+Launch vector_launch(int64_t n, int kp, int w, int num_sms) {
+    Launch L;
+    const int tpv = kp / w;
+    L.slots = tpv >= 256 ? 1 : 256 / tpv;
+    L.threads = tpv * L.slots;
+    const int64_t need = (n + L.slots - 1) / L.slots;
+    const int64_t g = (int64_t)num_sms * 8;
+    L.grid = (int)(need < g ? need : g);
+    if (L.grid < 1) L.grid = 1;
+    return L;
+}
+
+// Per-column partial sums of a thread owning W columns starting at c0.
+template <int W>
+__device__ __forceinline__ void column_partials_w(const double2 (&a)[W], const double (&b)[W], int kp, int slots,
+                                                  int c0, int slot, double2* partA, double* partB) {
+    extern __shared__ unsigned char smem_raw[];
+    double2* sA = reinterpret_cast<double2*>(smem_raw);
+    double* sB = reinterpret_cast<double*>(sA + slots * kp);
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        sA[slot * kp + c0 + u] = a[u];
+        sB[slot * kp + c0 + u] = b[u];
+    }
+    __syncthreads();
+    if (slot == 0) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            double2 ta = make_double2(0.0, 0.0);
+            double tb = 0.0;
+            for (int s = 0; s < slots; ++s) {
+                ta.x += sA[s * kp + c0 + u].x;
+                ta.y += sA[s * kp + c0 + u].y;
+                tb += sB[s * kp + c0 + u];
+            }
+            if (partA) partA[(int64_t)blockIdx.x * kp + c0 + u] = ta;
+            if (partB) partB[(int64_t)blockIdx.x * kp + c0 + u] = tb;
+        }
+    }
+}
+
+// q = A p and pq = p^T q; finaliser alpha = rho / pq.  One 16-byte load per
+// neighbour moves W columns; the grid keeps eight blocks per SM in flight.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T* __restrict__ q, int kp, int slots,
                                             ColState st) {
     using R = typename Elem<T>::R;
-    const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
-    const bool act = running(st, c);
-    T pq = ezero<T>();
-    if (act) {
-        const int nx = op.nx, ny = op.ny, nz = op.nz;
-        const int npen = nx * ny;
-        const int64_t sz = (int64_t)npen * kp;   // one z plane of the block
-        const int64_t sy = (int64_t)nx * kp;
-        for (int pen = blockIdx.x * slots + slot; pen < npen; pen += gridDim.x * slots) {
-            const int i = pen % nx, j = pen / nx;
-            const bool xm = i > 0, xp = i < nx - 1, ym = j > 0, yp = j < ny - 1;
-            int64_t e = (int64_t)pen * kp + c;
-            T pm = ezero<T>();
-            T pc = p[e];
-            T pn = nz > 1 ? p[e + sz] : ezero<T>();
-            R czm = 0;
-            int v = pen;
-#pragma unroll 2
-            for (int k = 0; k < nz; ++k) {
-                const T pnn = (k + 2 < nz) ? p[e + 2 * sz] : ezero<T>();
-                const R czc = (k < nz - 1) ? op.cz[v] : (R)0;
-                T acc = escale(op.dre[v], pc);
-                if (Elem<T>::cplx) acc = eadd(acc, emul_i(op.w, pc));
-                acc = esub(acc, escale(czm, pm));
-                acc = esub(acc, escale(czc, pn));
-                if (xm) acc = esub(acc, escale(op.cx[v - 1], p[e - kp]));
-                if (xp) acc = esub(acc, escale(op.cx[v], p[e + kp]));
-                if (ym) acc = esub(acc, escale(op.cy[v - nx], p[e - sy]));
-                if (yp) acc = esub(acc, escale(op.cy[v], p[e + sy]));
-                q[e] = acc;
-                pq = eadd(pq, emul(pc, acc));
-                pm = pc;
-                pc = pn;
-                pn = pnn;
-                czm = czc;
-                e += sz;
-                v += npen;
+    constexpr int W = Vec16<T>::W;
+    const int tpv = kp / W;
+    const int t = threadIdx.x % tpv, slot = threadIdx.x / tpv, c0 = t * W;
+    bool run[W];
+    bool any = false;
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        run[u] = running(st, c0 + u);
+        any = any || run[u];
+    }
+    T pq[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) pq[u] = ezero<T>();
+    if (any) {
+        const int nx = op.nx, ny = op.ny, nz = op.nz, nxy = nx * ny, n = nxy * nz;
+        const int64_t sy = (int64_t)nx * kp, sz = (int64_t)nxy * kp;
+        for (int v = blockIdx.x * slots + slot; v < n; v += gridDim.x * slots) {
+            const int kz = v / nxy, rem = v - kz * nxy, j = rem / nx, i = rem - j * nx;
+            const int64_t e = (int64_t)v * kp + c0;
+            const V16<T> pc = ld16(p + e);
+            const R d = op.dre[v];
+            V16<T> acc;
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                acc.e[u] = escale(d, pc.e[u]);
+                if (Elem<T>::cplx) acc.e[u] = eadd(acc.e[u], emul_i(op.w, pc.e[u]));
             }
+#define DOT_NB(cond, coef, off)                                                     \
+    if (cond) {                                                                     \
+        const R cf = (coef);                                                        \
+        const V16<T> nb = ld16(p + e + (off));                                      \
+        _Pragma("unroll") for (int u = 0; u < W; ++u) acc.e[u] = esub(acc.e[u], escale(cf, nb.e[u])); \
+    }
+            DOT_NB(i > 0, op.cx[v - 1], -(int64_t)kp)
+            DOT_NB(i < nx - 1, op.cx[v], (int64_t)kp)
+            DOT_NB(j > 0, op.cy[v - nx], -sy)
+            DOT_NB(j < ny - 1, op.cy[v], sy)
+            DOT_NB(kz > 0, op.cz[v - nxy], -sz)
+            DOT_NB(kz < nz - 1, op.cz[v], sz)
+#undef DOT_NB
+            st16(q + e, acc);
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+                if (run[u]) pq[u] = eadd(pq[u], emul(pc.e[u], acc.e[u]));
         }
     }
-    column_partials(ewide(pq), 0.0, kp, slots, c, slot, st.partA, nullptr);
+    double2 pa[W];
+    double pb[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        pa[u] = ewide(pq[u]);
+        pb[u] = 0.0;
+    }
+    column_partials_w<W>(pa, pb, kp, slots, c0, slot, st.partA, nullptr);
     if (arrive_last(st.counter)) {
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!running(st, cc)) continue;
@@ -267,31 +321,56 @@ __global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T
     }
 }
 
-// x~ += alpha p, r~ -= alpha q, rho' = r~^T M^{-1} r~, ||r~||^2.  Finaliser: pause the
-// column for a reliable update when ||r~|| reached the target or fell below
-// delta * max||r~||; otherwise beta = rho' / rho.
+// x~ += alpha p, r~ -= alpha q, rho' = r~^T M^{-1} r~, ||r~||^2 on the running
+// columns (the others are left untouched).  Finaliser: pause the column for a
+// reliable update when ||r~|| reached the target, fell below delta * max||r~|| or
+// went kRefreshEvery iterations without a refresh; otherwise beta = rho' / rho.
 template <typename T>
-__global__ void k_xr(Op<T> op, const T* __restrict__ p, const T* __restrict__ q, T* __restrict__ x,
-                     T* __restrict__ r, int64_t n, int kp, int slots, ColState st, double delta, int maxit) {
+__global__ void __launch_bounds__(256) k_xr(Op<T> op, const T* __restrict__ p, const T* __restrict__ q,
+                                            T* __restrict__ x, T* __restrict__ r, int64_t n, int kp, int slots,
+                                            ColState st, double delta, int maxit) {
     using R = typename Elem<T>::R;
-    const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
-    const bool act = running(st, c);
-    T rho = ezero<T>();
-    R rr = 0;
-    if (act) {
-        const T alpha = enarrow<T>(st.alpha[c]);
+    constexpr int W = Vec16<T>::W;
+    const int tpv = kp / W;
+    const int t = threadIdx.x % tpv, slot = threadIdx.x / tpv, c0 = t * W;
+    bool run[W];
+    bool any = false;
+    T alpha[W], rho[W];
+    R rr[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        run[u] = running(st, c0 + u);
+        any = any || run[u];
+        alpha[u] = run[u] ? enarrow<T>(st.alpha[c0 + u]) : ezero<T>();
+        rho[u] = ezero<T>();
+        rr[u] = 0;
+    }
+    if (any) {
         VOXEL_LOOP(v) {
-            const int64_t e = v * kp + c;
-            const T xv = eadd(x[e], emul(alpha, p[e]));
-            const T rv = esub(r[e], emul(alpha, q[e]));
-            x[e] = xv;
-            r[e] = rv;
-            const T z = emul(op.dinv[v], rv);
-            rho = eadd(rho, emul(rv, z));
-            rr += eabs2(rv);
+            const int64_t e = v * kp + c0;
+            const V16<T> pv = ld16(p + e), qv = ld16(q + e);
+            V16<T> xv = ld16(x + e), rv = ld16(r + e);
+            const T dv = op.dinv[v];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if (!run[u]) continue;
+                xv.e[u] = eadd(xv.e[u], emul(alpha[u], pv.e[u]));
+                rv.e[u] = esub(rv.e[u], emul(alpha[u], qv.e[u]));
+                rho[u] = eadd(rho[u], emul(rv.e[u], emul(dv, rv.e[u])));
+                rr[u] += eabs2(rv.e[u]);
+            }
+            st16(x + e, xv);
+            st16(r + e, rv);
         }
     }
-    column_partials(ewide(rho), (double)rr, kp, slots, c, slot, st.partA, st.partB);
+    double2 pa[W];
+    double pbv[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        pa[u] = ewide(rho[u]);
+        pbv[u] = (double)rr[u];
+    }
+    column_partials_w<W>(pa, pbv, kp, slots, c0, slot, st.partA, st.partB);
     if (arrive_last(st.counter)) {
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!running(st, cc)) continue;
@@ -332,16 +411,32 @@ __global__ void k_xr(Op<T> op, const T* __restrict__ p, const T* __restrict__ q,
     }
 }
 
-// p = M^{-1} r~ + beta p
+// p = M^{-1} r~ + beta p on the running columns.
 template <typename T>
-__global__ void k_p(Op<T> op, const T* __restrict__ r, T* __restrict__ p, int64_t n, int kp, int slots,
-                    ColState st) {
-    const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
-    if (!running(st, c)) return;
-    const T beta = enarrow<T>(st.beta[c]);
+__global__ void __launch_bounds__(256) k_p(Op<T> op, const T* __restrict__ r, T* __restrict__ p, int64_t n, int kp,
+                                           int slots, ColState st) {
+    constexpr int W = Vec16<T>::W;
+    const int tpv = kp / W;
+    const int t = threadIdx.x % tpv, slot = threadIdx.x / tpv, c0 = t * W;
+    bool run[W];
+    bool any = false;
+    T beta[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        run[u] = running(st, c0 + u);
+        any = any || run[u];
+        beta[u] = run[u] ? enarrow<T>(st.beta[c0 + u]) : ezero<T>();
+    }
+    if (!any) return;
     VOXEL_LOOP(v) {
-        const int64_t e = v * kp + c;
-        p[e] = eadd(emul(op.dinv[v], r[e]), emul(beta, p[e]));
+        const int64_t e = v * kp + c0;
+        const V16<T> rv = ld16(r + e);
+        V16<T> pv = ld16(p + e);
+        const T dv = op.dinv[v];
+#pragma unroll
+        for (int u = 0; u < W; ++u)
+            if (run[u]) pv.e[u] = eadd(emul(dv, rv.e[u]), emul(beta[u], pv.e[u]));
+        st16(p + e, pv);
     }
 }
 
@@ -516,21 +611,31 @@ cudaError_t solve_start(ElemKind inner, const OpRaw& o, const void* b64, void* x
 }
 
 cudaError_t kry_step(ElemKind inner, const OpRaw& o, void* x, void* r, void* p, void* q, int64_t n, int kp,
-                     const ColState& st, double delta, int maxit, bool with_p, const Launch& L, cudaStream_t s,
+                     const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv, cudaStream_t s,
                      cudaEvent_t* ev) {
     DOT_DISPATCH2(inner, {
         Op<T> op = make_op<T>(o);
+        const size_t sm = red_smem(Lv, kp);
         if (ev) cudaEventRecord(ev[0], s);
-        if (with_p) k_p<T><<<L.grid, L.threads, 0, s>>>(op, (const T*)r, (T*)p, n, kp, L.slots, st);
+        if (with_p) k_p<T><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, (T*)p, n, kp, Lv.slots, st);
         if (ev) cudaEventRecord(ev[1], s);
-        k_pq<T><<<L.grid, L.threads, red_smem(L, kp), s>>>(op, (const T*)p, (T*)q, kp, L.slots, st);
+        k_pq<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)p, (T*)q, kp, Lv.slots, st);
         if (ev) cudaEventRecord(ev[2], s);
-        k_xr<T><<<L.grid, L.threads, red_smem(L, kp), s>>>(op, (const T*)p, (const T*)q, (T*)x, (T*)r, n, kp,
-                                                            L.slots, st, delta, maxit);
+        k_xr<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)p, (const T*)q, (T*)x, (T*)r, n, kp, Lv.slots, st,
+                                                 delta, maxit);
         if (ev) cudaEventRecord(ev[3], s);
         (void)sizeof(T64);
     });
     return cudaGetLastError();
+}
+
+int vector_width(ElemKind inner) {
+    switch (inner) {
+        case EK_F32: return 4;
+        case EK_C64: return 2;
+        case EK_F64: return 2;
+        default: return 1;
+    }
 }
 
 cudaError_t solve_refresh(ElemKind inner, const OpRaw& o, const OpRaw& o64, const void* b64, void* x64, void* r64,

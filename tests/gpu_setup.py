@@ -37,3 +37,11 @@ def grad_err(g, ref_g, J, R_s, S):
     amplified by ||S|| / ||R_s||)."""
     scale = 2.0 * np.linalg.norm(J) * (np.linalg.norm(R_s) + np.linalg.norm(S))
     return float(np.linalg.norm(np.asarray(g) - np.asarray(ref_g)) / scale)
+
+
+def misfit_err(f, ref):
+    """Misfit error over max(f, 2 ||R_s|| ||S||): f = ||R_s||^2 with R_s = S - V^T M W moves by
+    at most 2 ||R_s|| ||dS|| under a perturbation dS, so near the data (R_s ~ 1% of S) the
+    relative error of f is the relative error of S amplified by ||S|| / ||R_s||."""
+    scale = max(ref["f"], 2.0 * np.linalg.norm(ref["R_s"]) * np.linalg.norm(ref["S"]))
+    return abs(f - ref["f"]) / scale

