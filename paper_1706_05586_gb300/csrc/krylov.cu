@@ -76,20 +76,71 @@ __device__ __forceinline__ bool arrive_last(unsigned* counter) {
     return am_last != 0;
 }
 
-__device__ __forceinline__ void sum_partials(const double2* partA, const double* partB, int kp, int cc,
-                                             double2* a, double* b) {
-    double2 ra = make_double2(0.0, 0.0);
-    double rb = 0.0;
-    for (int g = 0; g < (int)gridDim.x; ++g) {
-        if (partA) {
-            double2 t = __ldcg(&partA[(int64_t)g * kp + cc]);
-            ra.x += t.x;
-            ra.y += t.y;
+// Totals of the per-block partial sums, computed by every thread of the last block:
+// tpc = blockDim / kp threads share a column, each summing a fixed strided subset of
+// the blocks with eight independent accumulators, and the subsets are combined in a
+// fixed order, so the result does not depend on scheduling.  Returns pointers to the
+// kp totals in shared memory (valid until the block exits).
+__device__ void block_sums(const double2* partA, const double* partB, int kp, const double2** outA,
+                           const double** outB) {
+    extern __shared__ unsigned char smem_raw[];
+    double2* sA = reinterpret_cast<double2*>(smem_raw);
+    const int tpc = max(1, (int)blockDim.x / kp);
+    double* sB = reinterpret_cast<double*>(sA + tpc * kp);
+    const int G = gridDim.x;
+    for (int t = threadIdx.x; t < kp * tpc; t += blockDim.x) {
+        const int cc = t % kp, q = t / kp;
+        double2 a[8];
+        double b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            a[u] = make_double2(0.0, 0.0);
+            b[u] = 0.0;
         }
-        if (partB) rb += __ldcg(&partB[(int64_t)g * kp + cc]);
+        int g = q;
+        for (; g + 7 * tpc < G; g += 8 * tpc) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t o = (int64_t)(g + u * tpc) * kp + cc;
+                if (partA) {
+                    const double2 x = __ldcg(&partA[o]);
+                    a[u].x += x.x;
+                    a[u].y += x.y;
+                }
+                if (partB) b[u] += __ldcg(&partB[o]);
+            }
+        }
+        for (; g < G; g += tpc) {
+            const int64_t o = (int64_t)g * kp + cc;
+            if (partA) {
+                const double2 x = __ldcg(&partA[o]);
+                a[0].x += x.x;
+                a[0].y += x.y;
+            }
+            if (partB) b[0] += __ldcg(&partB[o]);
+        }
+        double2 ta = make_double2(0.0, 0.0);
+        double tb = 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            ta.x += a[u].x;
+            ta.y += a[u].y;
+            tb += b[u];
+        }
+        sA[q * kp + cc] = ta;
+        sB[q * kp + cc] = tb;
     }
-    *a = ra;
-    *b = rb;
+    __syncthreads();
+    for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
+        for (int q = 1; q < tpc; ++q) {
+            sA[cc].x += sA[q * kp + cc].x;
+            sA[cc].y += sA[q * kp + cc].y;
+            sB[cc] += sB[q * kp + cc];
+        }
+    }
+    __syncthreads();
+    *outA = sA;
+    *outB = sB;
 }
 
 // Column counters written by the finalisers: active columns and columns paused for
@@ -134,10 +185,12 @@ __global__ void k_start_norm(const T64* __restrict__ b, T64* __restrict__ x64, i
     }
     column_partials(make_double2(0.0, 0.0), bb, kp, slots, c, slot, nullptr, st.partB);
     if (arrive_last(st.counter)) {
+        const double2* totA;
+        const double* totB;
+        block_sums(nullptr, st.partB, kp, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-            double2 a;
-            double bsum;
-            sum_partials(nullptr, st.partB, kp, cc, &a, &bsum);
+            const double2 a = totA[cc];
+            const double bsum = totB[cc];
             const bool fin = isfinite(bsum);
             st.bb64[cc] = bsum;
             st.rr64[cc] = bsum;
@@ -178,11 +231,13 @@ __global__ void k_start_inner(Op<T> op, const T64* __restrict__ b, T* __restrict
     }
     column_partials(ewide(rho), (double)rr, kp, slots, c, slot, st.partA, st.partB);
     if (arrive_last(st.counter)) {
+        const double2* totA;
+        const double* totB;
+        block_sums(st.partA, st.partB, kp, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!st.active[cc]) continue;
-            double2 a;
-            double rsum;
-            sum_partials(st.partA, st.partB, kp, cc, &a, &rsum);
+            const double2 a = totA[cc];
+            const double rsum = totB[cc];
             st.rho[cc] = a;
             st.rr[cc] = rsum;
             st.maxr[cc] = sqrt(rsum);
@@ -304,11 +359,13 @@ __global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T
     }
     column_partials_w<W>(pa, pb, kp, slots, c0, slot, st.partA, nullptr);
     if (arrive_last(st.counter)) {
+        const double2* totA;
+        const double* totB;
+        block_sums(st.partA, nullptr, kp, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!running(st, cc)) continue;
-            double2 a;
-            double unused;
-            sum_partials(st.partA, nullptr, kp, cc, &a, &unused);
+            const double2 a = totA[cc];
+            const double unused = totB[cc];
             if (!zfinite(a) || (a.x == 0.0 && a.y == 0.0)) {
                 st.status[cc] = DOT_EBREAKDOWN;
                 st.active[cc] = 0;
@@ -372,11 +429,13 @@ __global__ void __launch_bounds__(256) k_xr(Op<T> op, const T* __restrict__ p, c
     }
     column_partials_w<W>(pa, pbv, kp, slots, c0, slot, st.partA, st.partB);
     if (arrive_last(st.counter)) {
+        const double2* totA;
+        const double* totB;
+        block_sums(st.partA, st.partB, kp, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!running(st, cc)) continue;
-            double2 a;
-            double rsum;
-            sum_partials(st.partA, st.partB, kp, cc, &a, &rsum);
+            const double2 a = totA[cc];
+            const double rsum = totB[cc];
             const int it = st.iters[cc] + 1;
             st.iters[cc] = it;
             st.rr[cc] = rsum;
@@ -477,12 +536,14 @@ __global__ void k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64
     }
     column_partials(make_double2(0.0, 0.0), rr, kp, slots, c, slot, nullptr, st.partB);
     if (arrive_last(st.counter)) {
+        const double2* totA;
+        const double* totB;
+        block_sums(nullptr, st.partB, kp, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             const bool s2 = all ? true : (st.active[cc] && st.upd[cc]);
             if (!s2) continue;
-            double2 a;
-            double rsum;
-            sum_partials(nullptr, st.partB, kp, cc, &a, &rsum);
+            const double2 a = totA[cc];
+            const double rsum = totB[cc];
             st.rr64[cc] = rsum;
             if (all) continue;
             st.updates[cc] += 1;
@@ -532,11 +593,13 @@ __global__ void k_refresh(Op<T> op, const T64* __restrict__ r64, T* __restrict__
     }
     column_partials(ewide(rho), (double)rr, kp, slots, c, slot, st.partA, st.partB);
     if (arrive_last(st.counter)) {
+        const double2* totA;
+        const double* totB;
+        block_sums(st.partA, st.partB, kp, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!(st.active[cc] && st.upd[cc])) continue;
-            double2 a;
-            double rsum;
-            sum_partials(st.partA, st.partB, kp, cc, &a, &rsum);
+            const double2 a = totA[cc];
+            const double rsum = totB[cc];
             st.upd[cc] = 0;
             const double2 rho_old = st.rho[cc];
             if (!zfinite(a) || !isfinite(rsum) || (rho_old.x == 0.0 && rho_old.y == 0.0)) {
