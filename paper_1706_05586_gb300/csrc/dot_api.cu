@@ -221,7 +221,7 @@ int ensure_coefficients(dot_ctx* c) {
 
 int alloc_colstate(dot_ctx* c, int kp, int max_grid, ColState* st) {
     const size_t n16 = (size_t)kp * 16, n8 = (size_t)kp * 8, n4 = (size_t)kp * 4;
-    const size_t bytes = 3 * n16 + 7 * n8 + 6 * n4 + 64;
+    const size_t bytes = 4 * n16 + 7 * n8 + 6 * n4 + 64;
     TRY(ensure(c->colbuf, bytes));
     TRY(ensure(c->partA, (size_t)max_grid * kp * 16));
     TRY(ensure(c->partB, (size_t)max_grid * kp * 8));
@@ -233,6 +233,7 @@ int alloc_colstate(dot_ctx* c, int kp, int max_grid, ColState* st) {
         return r;
     };
     st->rho = reinterpret_cast<double2*>(take(n16));
+    st->rho_prev = reinterpret_cast<double2*>(take(n16));
     st->alpha = reinterpret_cast<double2*>(take(n16));
     st->beta = reinterpret_cast<double2*>(take(n16));
     st->rr = reinterpret_cast<double*>(take(n8));

@@ -11,6 +11,7 @@ namespace dotk {
 // The recurrence runs on r~ = r / scale; the FP64 solution and true residual are separate.
 struct ColState {
     double2* rho;      // r~^T M^{-1} r~ (bilinear; imaginary part 0 in real arithmetic)
+    double2* rho_prev; // rho of the previous iteration (the denominator of beta)
     double2* alpha;
     double2* beta;
     double* rr;        // ||r~||^2 of the recurrence

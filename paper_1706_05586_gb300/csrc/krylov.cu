@@ -81,8 +81,8 @@ __device__ __forceinline__ bool arrive_last(unsigned* counter) {
 // the blocks with eight independent accumulators, and the subsets are combined in a
 // fixed order, so the result does not depend on scheduling.  Returns pointers to the
 // kp totals in shared memory (valid until the block exits).
-__device__ void block_sums(const double2* partA, const double* partB, int kp, const double2** outA,
-                           const double** outB) {
+__device__ __noinline__ void block_sums(const double2* partA, const double* partB, int kp, const double2** outA,
+                                        const double** outB) {
     extern __shared__ unsigned char smem_raw[];
     double2* sA = reinterpret_cast<double2*>(smem_raw);
     const int tpc = max(1, (int)blockDim.x / kp);
@@ -90,42 +90,41 @@ __device__ void block_sums(const double2* partA, const double* partB, int kp, co
     const int G = gridDim.x;
     for (int t = threadIdx.x; t < kp * tpc; t += blockDim.x) {
         const int cc = t % kp, q = t / kp;
-        double2 a[8];
-        double b[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            a[u] = make_double2(0.0, 0.0);
-            b[u] = 0.0;
-        }
-        int g = q;
-        for (; g + 7 * tpc < G; g += 8 * tpc) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t o = (int64_t)(g + u * tpc) * kp + cc;
-                if (partA) {
-                    const double2 x = __ldcg(&partA[o]);
-                    a[u].x += x.x;
-                    a[u].y += x.y;
-                }
-                if (partB) b[u] += __ldcg(&partB[o]);
-            }
-        }
-        for (; g < G; g += tpc) {
-            const int64_t o = (int64_t)g * kp + cc;
-            if (partA) {
-                const double2 x = __ldcg(&partA[o]);
-                a[0].x += x.x;
-                a[0].y += x.y;
-            }
-            if (partB) b[0] += __ldcg(&partB[o]);
-        }
+        // two passes with four independent accumulators each keep the register
+        // footprint of this rarely-run code below that of the kernels' main loops
         double2 ta = make_double2(0.0, 0.0);
+        if (partA) {
+            double2 a0 = ta, a1 = ta, a2 = ta, a3 = ta;
+            int g = q;
+            for (; g + 3 * tpc < G; g += 4 * tpc) {
+                const double2 x0 = __ldcg(&partA[(int64_t)g * kp + cc]);
+                const double2 x1 = __ldcg(&partA[(int64_t)(g + tpc) * kp + cc]);
+                const double2 x2 = __ldcg(&partA[(int64_t)(g + 2 * tpc) * kp + cc]);
+                const double2 x3 = __ldcg(&partA[(int64_t)(g + 3 * tpc) * kp + cc]);
+                a0.x += x0.x; a0.y += x0.y;
+                a1.x += x1.x; a1.y += x1.y;
+                a2.x += x2.x; a2.y += x2.y;
+                a3.x += x3.x; a3.y += x3.y;
+            }
+            for (; g < G; g += tpc) {
+                const double2 x0 = __ldcg(&partA[(int64_t)g * kp + cc]);
+                a0.x += x0.x;
+                a0.y += x0.y;
+            }
+            ta = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+        }
         double tb = 0.0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            ta.x += a[u].x;
-            ta.y += a[u].y;
-            tb += b[u];
+        if (partB) {
+            double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+            int g = q;
+            for (; g + 3 * tpc < G; g += 4 * tpc) {
+                b0 += __ldcg(&partB[(int64_t)g * kp + cc]);
+                b1 += __ldcg(&partB[(int64_t)(g + tpc) * kp + cc]);
+                b2 += __ldcg(&partB[(int64_t)(g + 2 * tpc) * kp + cc]);
+                b3 += __ldcg(&partB[(int64_t)(g + 3 * tpc) * kp + cc]);
+            }
+            for (; g < G; g += tpc) b0 += __ldcg(&partB[(int64_t)g * kp + cc]);
+            tb = (b0 + b1) + (b2 + b3);
         }
         sA[q * kp + cc] = ta;
         sB[q * kp + cc] = tb;
@@ -445,6 +444,7 @@ __global__ void __launch_bounds__(256) k_xr(Op<T> op, const T* __restrict__ p, c
                 continue;
             }
             const double mr = st.maxr[cc];
+            st.rho_prev[cc] = st.rho[cc];
             const int since = st.since[cc] + 1;
             st.since[cc] = since;
             // refresh at the target, after a drop by delta, at the iteration budget, and (in
@@ -500,22 +500,24 @@ __global__ void __launch_bounds__(256) k_p(Op<T> op, const T* __restrict__ r, T*
 }
 
 // ------------------------------------------------------------ reliable update
-// x64 += s x~, x~ = 0 on the paused columns (every column when all != 0).
+// x64 += s x~, x~ = 0 on the active columns (every column when all != 0).
 template <typename T64, typename T>
-__global__ void k_promote(T64* __restrict__ x64, T* __restrict__ x, int64_t n, int kp, ColState st, int all) {
-    const int64_t total = n * kp;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e % kp);
-        if (!(all || (st.active[c] && st.upd[c]))) continue;
-        const double s = st.scale[c];
+__global__ void k_promote(T64* __restrict__ x64, T* __restrict__ x, int64_t n, int kp, int slots, ColState st,
+                          int all) {
+    const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
+    if (!(all || st.active[c])) return;
+    const double s = st.scale[c];
+    VOXEL_LOOP(v) {
+        const int64_t e = v * kp + c;
         const double2 d = ewide(x[e]);
         x64[e] = eadd(x64[e], enarrow<T64>(make_double2(s * d.x, s * d.y)));
         x[e] = ezero<T>();
     }
 }
 
-// r64 = b - A x64 in FP64 on the paused columns (every column when all != 0).
+// r64 = b - A x64 in FP64 on the active columns (every column when all != 0).  A
+// refresh round serves every active column at once: one FP64 pass costs the same
+// for one column as for all, and refreshing a column early is always valid.
 // Finaliser (update mode): converged when ||r64|| <= rtol ||b||, stopped when the
 // iteration budget is spent, otherwise the new scale s' = ||r64||, ratio = s / s',
 // and the scaled target tol2 = rtol^2 ||b||^2 / s'^2.
@@ -524,7 +526,7 @@ __global__ void k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64
                                 T64* __restrict__ r64, int64_t n, int kp, int slots, ColState st, double rtol,
                                 int maxit, int all) {
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
-    const bool sel = all ? true : (st.active[c] && st.upd[c]);
+    const bool sel = all ? true : (st.active[c] != 0);
     double rr = 0.0;
     if (sel) {
         VOXEL_LOOP(v) {
@@ -540,7 +542,7 @@ __global__ void k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64
         const double* totB;
         block_sums(nullptr, st.partB, kp, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-            const bool s2 = all ? true : (st.active[cc] && st.upd[cc]);
+            const bool s2 = all ? true : (st.active[cc] != 0);
             if (!s2) continue;
             const double2 a = totA[cc];
             const double rsum = totB[cc];
@@ -571,14 +573,15 @@ __global__ void k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64
     }
 }
 
-// r~ = r64 / s' on the refreshed columns; rho' = r~^T M^{-1} r~.  The search
-// direction is kept in the old scale, so beta = (rho' / rho) / ratio carries it over.
+// r~ = r64 / s' on the refreshed (active) columns; rho' = r~^T M^{-1} r~.  The search
+// direction is kept in the old scale, so beta = (rho' / rho_prev) / ratio carries it
+// over, where rho_prev is the rho of the iteration that produced the replaced residual.
 template <typename T, typename T64>
 __global__ void k_refresh(Op<T> op, const T64* __restrict__ r64, T* __restrict__ r, int64_t n, int kp, int slots,
                           ColState st) {
     using R = typename Elem<T>::R;
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
-    const bool sel = st.active[c] && st.upd[c];
+    const bool sel = st.active[c] != 0;
     T rho = ezero<T>();
     R rr = 0;
     if (sel) {
@@ -597,11 +600,11 @@ __global__ void k_refresh(Op<T> op, const T64* __restrict__ r64, T* __restrict__
         const double* totB;
         block_sums(st.partA, st.partB, kp, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-            if (!(st.active[cc] && st.upd[cc])) continue;
+            if (!st.active[cc]) continue;
             const double2 a = totA[cc];
             const double rsum = totB[cc];
             st.upd[cc] = 0;
-            const double2 rho_old = st.rho[cc];
+            const double2 rho_old = st.rho_prev[cc];
             if (!zfinite(a) || !isfinite(rsum) || (rho_old.x == 0.0 && rho_old.y == 0.0)) {
                 st.status[cc] = DOT_EBREAKDOWN;
                 st.active[cc] = 0;
@@ -704,9 +707,9 @@ int vector_width(ElemKind inner) {
 cudaError_t solve_refresh(ElemKind inner, const OpRaw& o, const OpRaw& o64, const void* b64, void* x64, void* r64,
                           void* x, void* r, int64_t n, int kp, const ColState& st, double rtol, int maxit,
                           const Launch& L, int num_sms, cudaStream_t s) {
-    const int ge = grid_elems(n * kp, num_sms * 16);
+    (void)num_sms;
     DOT_DISPATCH2(inner, {
-        k_promote<T64, T><<<ge, 256, 0, s>>>((T64*)x64, (T*)x, n, kp, st, 0);
+        k_promote<T64, T><<<L.grid, L.threads, 0, s>>>((T64*)x64, (T*)x, n, kp, L.slots, st, 0);
         k_true_residual<T64><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<T64>(o64), (const T64*)b64,
                                                                         (const T64*)x64, (T64*)r64, n, kp, L.slots,
                                                                         st, rtol, maxit, 0);
@@ -718,9 +721,9 @@ cudaError_t solve_refresh(ElemKind inner, const OpRaw& o, const OpRaw& o64, cons
 
 cudaError_t solve_finish(ElemKind inner, const OpRaw& o64, const void* b64, void* x64, void* r64, void* x, int64_t n,
                          int kp, const ColState& st, bool residual, const Launch& L, int num_sms, cudaStream_t s) {
-    const int ge = grid_elems(n * kp, num_sms * 16);
+    (void)num_sms;
     DOT_DISPATCH2(inner, {
-        k_promote<T64, T><<<ge, 256, 0, s>>>((T64*)x64, (T*)x, n, kp, st, 1);
+        k_promote<T64, T><<<L.grid, L.threads, 0, s>>>((T64*)x64, (T*)x, n, kp, L.slots, st, 1);
         if (residual)
             k_true_residual<T64><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<T64>(o64), (const T64*)b64,
                                                                             (const T64*)x64, (T64*)r64, n, kp,
