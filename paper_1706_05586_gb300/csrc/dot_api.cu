@@ -92,7 +92,7 @@ struct dot_ctx {
     double mu_in = 0, mu_out = 0, cut = 0, eps = 1, gamma = 0;
 
     bool coef_valid = false;
-    DevBuf cx, cy, cz, dre, dinv64, cx32, cy32, cz32, dre32, dinv32;
+    DevBuf cf64, dinv64, cf32, dinv32;  // packed (cx, cy, cz, dre) and Jacobi inverse diagonal
 
     int ns = 0, nd = 0;
     DevBuf rpB, ciB, vB, rpC, ciC, vC, cpC, rwC, vCc;
@@ -172,10 +172,7 @@ int kp_limit_check(dot_ctx* c) {
 
 OpRaw op64(const dot_ctx* c) {
     OpRaw o;
-    o.cx = c->cx.p;
-    o.cy = c->cy.p;
-    o.cz = c->cz.p;
-    o.dre = c->dre.p;
+    o.cf = c->cf64.p;
     o.dinv = c->dinv64.p;
     o.w = c->w;
     o.nx = c->nx;
@@ -185,10 +182,7 @@ OpRaw op64(const dot_ctx* c) {
 }
 OpRaw op32(const dot_ctx* c) {
     OpRaw o = op64(c);
-    o.cx = c->cx32.p;
-    o.cy = c->cy32.p;
-    o.cz = c->cz32.p;
-    o.dre = c->dre32.p;
+    o.cf = c->cf32.p;
     o.dinv = c->dinv32.p;
     return o;
 }
@@ -206,14 +200,12 @@ int ensure_coefficients(dot_ctx* c) {
         CK(pals_eval(c->p.as<double>(), c->m0, c->mu_in, c->mu_out, c->cut, c->eps, c->gamma, c->nx, c->ny, c->nz,
                      c->h, c->phi.as<double>(), c->mu.as<double>(), c->wdmu.as<double>(), c->s));
     }
-    for (DevBuf* b : {&c->cx, &c->cy, &c->cz, &c->dre}) TRY(ensure(*b, n * 8));
-    for (DevBuf* b : {&c->cx32, &c->cy32, &c->cz32, &c->dre32}) TRY(ensure(*b, n * 4));
+    TRY(ensure(c->cf64, n * 32));
+    TRY(ensure(c->cf32, n * 16));
     TRY(ensure(c->dinv64, n * 16));
     TRY(ensure(c->dinv32, n * 8));
-    CK(build_coefficients(c->D.as<double>(), c->mu.as<double>(), c->nx, c->ny, c->nz, c->h, c->bc, c->w,
-                          c->cx.as<double>(), c->cy.as<double>(), c->cz.as<double>(), c->dre.as<double>(), c->dinv64.p,
-                          cplx(c), c->cx32.as<float>(), c->cy32.as<float>(), c->cz32.as<float>(),
-                          c->dre32.as<float>(), c->dinv32.p, c->s));
+    CK(build_coefficients(c->D.as<double>(), c->mu.as<double>(), c->nx, c->ny, c->nz, c->h, c->bc, c->w, c->cf64.p,
+                          c->dinv64.p, cplx(c), c->cf32.p, c->dinv32.p, c->s));
     count(c, c->mu_mode == 2 ? 2 : 1);
     c->coef_valid = true;
     return DOT_OK;
@@ -553,8 +545,7 @@ int dot_destroy(dot_ctx* c) {
     if (!c) return DOT_OK;
     cudaSetDevice(c->device);
     if (c->s) cudaStreamSynchronize(c->s);
-    DevBuf* bufs[] = {&c->D, &c->mu, &c->phi, &c->wdmu, &c->p, &c->cx, &c->cy, &c->cz, &c->dre, &c->dinv64,
-                      &c->cx32, &c->cy32, &c->cz32, &c->dre32, &c->dinv32, &c->rpB, &c->ciB, &c->vB, &c->rpC,
+    DevBuf* bufs[] = {&c->D, &c->mu, &c->phi, &c->wdmu, &c->p, &c->cf64, &c->dinv64, &c->cf32, &c->dinv32, &c->rpB, &c->ciB, &c->vB, &c->rpC,
                       &c->ciC, &c->vC, &c->cpC, &c->rwC, &c->vCc, &c->W, &c->V, &c->M, &c->MW, &c->P, &c->b64,
                       &c->x64, &c->r64, &c->xi, &c->ri, &c->pi, &c->qi, &c->colbuf, &c->partA, &c->partB, &c->Tm,
                       &c->S, &c->Rs, &c->f, &c->gmu, &c->gp, &c->J, &c->tmp};

@@ -36,10 +36,7 @@ struct ColState {
 
 // Raw operator coefficients in one precision.
 struct OpRaw {
-    const void* cx;
-    const void* cy;
-    const void* cz;
-    const void* dre;
+    const void* cf;    // packed (cx, cy, cz, dre) per voxel
     const void* dinv;  // element type: real or complex of the same precision
     double w;
     int nx, ny, nz;
@@ -85,10 +82,11 @@ cudaError_t op_apply(ElemKind ek, const OpRaw& op, const void* x, void* y, int64
 cudaError_t pals_eval(const double* p, int m0, double mu_in, double mu_out, double c, double eps,
                       double gamma, int nx, int ny, int nz, double h, double* phi, double* mu,
                       double* wdmu, cudaStream_t s);
+// Packed coefficients (cx, cy, cz, dre) per voxel in FP64 (cf64) and FP32 (cf32),
+// and the Jacobi inverse diagonal in both precisions.
 cudaError_t build_coefficients(const double* D, const double* mu, int nx, int ny, int nz, double h,
-                               const int bc[6], double w, double* cx, double* cy, double* cz,
-                               double* dre, void* dinv64, bool cplx, float* cx32, float* cy32,
-                               float* cz32, float* dre32, void* dinv32, cudaStream_t s);
+                               const int bc[6], double w, void* cf64, void* dinv64, bool cplx, void* cf32,
+                               void* dinv32, cudaStream_t s);
 cudaError_t build_rhs(bool cplx, const int64_t* rowptrB, const int32_t* colB, const double* valB,
                       const double* W, int ns, int ls, const int64_t* rowptrC, const int32_t* colC,
                       const double* valC, const double* V, int nd, int ld, int64_t n, int kp, void* X,

@@ -113,17 +113,20 @@ __device__ __forceinline__ void st16(T* __restrict__ p, const V16<T>& v) {
 }
 
 // ---------------------------------------------------------------- operator
-// Coefficients of (A(mu) + i w I), per unit volume:
-//   (A u)_v = dre_v u_v + i w u_v - sum_faces cf * u_nb
-// cx[v] couples v and v+1 (0 on the +x boundary), cy[v] v and v+nx, cz[v] v and v+nx*ny.
-// dinv = 1 / (dre + i w) is the Jacobi preconditioner, stored in the element type.
+// Coefficients of (A(mu) + i w I), per unit volume, packed per voxel:
+//   (A u)_v = dre_v u_v + i w u_v - sum_faces c_f u_nb
+// cx couples v and v+1 (0 on the +x boundary), cy v and v+nx, cz v and v+nx*ny; one
+// aligned load brings a voxel's four coefficients.  dinv = 1 / (dre + i w) is the
+// Jacobi preconditioner, stored in the element type.
+template <typename R>
+struct alignas(4 * sizeof(R)) Cf4 {
+    R cx, cy, cz, dre;
+};
+
 template <typename T>
 struct Op {
     using R = typename Elem<T>::R;
-    const R* cx;
-    const R* cy;
-    const R* cz;
-    const R* dre;
+    const Cf4<R>* cf;
     const T* dinv;
     R w;
     int nx, ny, nz;
@@ -141,16 +144,16 @@ __device__ __forceinline__ T apply_at(const Op<T>& op, const T* __restrict__ x, 
     const int j = rem / op.nx;
     const int i = rem - j * op.nx;
     const int64_t e = v * kp + c;
+    const Cf4<R> cv = op.cf[vi];
     T xc = x[e];
-    T acc = escale(op.dre[v], xc);
+    T acc = escale(cv.dre, xc);
     if (Elem<T>::cplx) acc = eadd(acc, emul_i(op.w, xc));
-    if (i > 0)          acc = esub(acc, escale(op.cx[v - 1], x[e - kp]));
-    if (i < op.nx - 1)  acc = esub(acc, escale(op.cx[v], x[e + kp]));
-    if (j > 0)          acc = esub(acc, escale(op.cy[v - op.nx], x[e - (int64_t)op.nx * kp]));
-    if (j < op.ny - 1)  acc = esub(acc, escale(op.cy[v], x[e + (int64_t)op.nx * kp]));
-    if (kz > 0)         acc = esub(acc, escale(op.cz[v - nxy], x[e - (int64_t)nxy * kp]));
-    if (kz < op.nz - 1) acc = esub(acc, escale(op.cz[v], x[e + (int64_t)nxy * kp]));
-    (void)sizeof(R);
+    if (i > 0)          acc = esub(acc, escale(op.cf[vi - 1].cx, x[e - kp]));
+    if (i < op.nx - 1)  acc = esub(acc, escale(cv.cx, x[e + kp]));
+    if (j > 0)          acc = esub(acc, escale(op.cf[vi - op.nx].cy, x[e - (int64_t)op.nx * kp]));
+    if (j < op.ny - 1)  acc = esub(acc, escale(cv.cy, x[e + (int64_t)op.nx * kp]));
+    if (kz > 0)         acc = esub(acc, escale(op.cf[vi - nxy].cz, x[e - (int64_t)nxy * kp]));
+    if (kz < op.nz - 1) acc = esub(acc, escale(cv.cz, x[e + (int64_t)nxy * kp]));
     return acc;
 }
 

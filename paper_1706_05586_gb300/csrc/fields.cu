@@ -97,9 +97,8 @@ __device__ __forceinline__ double bnd_coef(int flag, double Dc, double h) {
 struct Bc6 { int f[6]; };
 
 __global__ void k_coefficients(const double* __restrict__ D, const double* __restrict__ mu, int nx, int ny, int nz,
-                               double h, Bc6 bc, double w, double* cx, double* cy, double* cz, double* dre,
-                               double* dinv64, int cplx, float* cx32, float* cy32, float* cz32, float* dre32,
-                               float* dinv32) {
+                               double h, Bc6 bc, double w, Cf4<double>* __restrict__ cf64, double* dinv64, int cplx,
+                               Cf4<float>* __restrict__ cf32, float* dinv32) {
     const int64_t n = (int64_t)nx * ny * nz;
     const int64_t nxy = (int64_t)nx * ny;
     const double h2 = h * h;
@@ -116,14 +115,18 @@ __global__ void k_coefficients(const double* __restrict__ D, const double* __res
         d += j < ny - 1 ? fyp : bnd_coef(bc.f[3], Dv, h);
         d += k > 0 ? face_coef(D[v - nxy], Dv, h2) : bnd_coef(bc.f[4], Dv, h);
         d += k < nz - 1 ? fzp : bnd_coef(bc.f[5], Dv, h);
-        cx[v] = fxp;
-        cy[v] = fyp;
-        cz[v] = fzp;
-        dre[v] = d;
-        cx32[v] = (float)fxp;
-        cy32[v] = (float)fyp;
-        cz32[v] = (float)fzp;
-        dre32[v] = (float)d;
+        Cf4<double> c64;
+        c64.cx = fxp;
+        c64.cy = fyp;
+        c64.cz = fzp;
+        c64.dre = d;
+        cf64[v] = c64;
+        Cf4<float> c32;
+        c32.cx = (float)fxp;
+        c32.cy = (float)fyp;
+        c32.cz = (float)fzp;
+        c32.dre = (float)d;
+        cf32[v] = c32;
         if (cplx) {
             // 1 / (d + i w) = (d - i w) / (d^2 + w^2)
             const double den = d * d + w * w;
@@ -138,13 +141,13 @@ __global__ void k_coefficients(const double* __restrict__ D, const double* __res
 }
 
 cudaError_t build_coefficients(const double* D, const double* mu, int nx, int ny, int nz, double h, const int bc[6],
-                               double w, double* cx, double* cy, double* cz, double* dre, void* dinv64, bool cplx,
-                               float* cx32, float* cy32, float* cz32, float* dre32, void* dinv32, cudaStream_t s) {
+                               double w, void* cf64, void* dinv64, bool cplx, void* cf32, void* dinv32,
+                               cudaStream_t s) {
     Bc6 b;
     for (int f = 0; f < 6; ++f) b.f[f] = bc[f];
     const int64_t n = (int64_t)nx * ny * nz;
-    k_coefficients<<<grid_for(n, 256), 256, 0, s>>>(D, mu, nx, ny, nz, h, b, w, cx, cy, cz, dre, (double*)dinv64,
-                                                    cplx ? 1 : 0, cx32, cy32, cz32, dre32, (float*)dinv32);
+    k_coefficients<<<grid_for(n, 256), 256, 0, s>>>(D, mu, nx, ny, nz, h, b, w, (Cf4<double>*)cf64, (double*)dinv64,
+                                                    cplx ? 1 : 0, (Cf4<float>*)cf32, (float*)dinv32);
     return cudaGetLastError();
 }
 

@@ -300,53 +300,51 @@ __device__ __forceinline__ void column_partials_w(const double2 (&a)[W], const d
 // q = A p and pq = p^T q; finaliser alpha = rho / pq.  One 16-byte load per
 // neighbour moves W columns; the grid keeps eight blocks per SM in flight.
 template <typename T>
-__global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T* __restrict__ q, int kp, int slots,
-                                            ColState st) {
+__global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T* __restrict__ q, int kp,
+                                               int slots, ColState st) {
     using R = typename Elem<T>::R;
     constexpr int W = Vec16<T>::W;
     const int tpv = kp / W;
     const int t = threadIdx.x % tpv, slot = threadIdx.x / tpv, c0 = t * W;
-    bool run[W];
     bool any = false;
 #pragma unroll
-    for (int u = 0; u < W; ++u) {
-        run[u] = running(st, c0 + u);
-        any = any || run[u];
-    }
+    for (int u = 0; u < W; ++u) any = any || running(st, c0 + u);
+    // pq is accumulated for every column of the vector; the finaliser reads only the
+    // running ones (a paused or stopped column's q is scratch)
     T pq[W];
 #pragma unroll
     for (int u = 0; u < W; ++u) pq[u] = ezero<T>();
     if (any) {
-        const int nx = op.nx, ny = op.ny, nz = op.nz, nxy = nx * ny, n = nxy * nz;
-        const int64_t sy = (int64_t)nx * kp, sz = (int64_t)nxy * kp;
+        const int nx = op.nx, nxy = nx * op.ny, n = nxy * op.nz;
+        const T* __restrict__ pp = p + c0;
+        T* __restrict__ qq = q + c0;
         for (int v = blockIdx.x * slots + slot; v < n; v += gridDim.x * slots) {
             const int kz = v / nxy, rem = v - kz * nxy, j = rem / nx, i = rem - j * nx;
-            const int64_t e = (int64_t)v * kp + c0;
-            const V16<T> pc = ld16(p + e);
-            const R d = op.dre[v];
+            const int64_t e = (int64_t)v * kp;
+            const V16<T> pc = ld16(pp + e);
+            const Cf4<R> cv = op.cf[v];
             V16<T> acc;
 #pragma unroll
             for (int u = 0; u < W; ++u) {
-                acc.e[u] = escale(d, pc.e[u]);
+                acc.e[u] = escale(cv.dre, pc.e[u]);
                 if (Elem<T>::cplx) acc.e[u] = eadd(acc.e[u], emul_i(op.w, pc.e[u]));
             }
 #define DOT_NB(cond, coef, off)                                                     \
     if (cond) {                                                                     \
         const R cf = (coef);                                                        \
-        const V16<T> nb = ld16(p + e + (off));                                      \
+        const V16<T> nb = ld16(pp + e + (off));                                     \
         _Pragma("unroll") for (int u = 0; u < W; ++u) acc.e[u] = esub(acc.e[u], escale(cf, nb.e[u])); \
     }
-            DOT_NB(i > 0, op.cx[v - 1], -(int64_t)kp)
-            DOT_NB(i < nx - 1, op.cx[v], (int64_t)kp)
-            DOT_NB(j > 0, op.cy[v - nx], -sy)
-            DOT_NB(j < ny - 1, op.cy[v], sy)
-            DOT_NB(kz > 0, op.cz[v - nxy], -sz)
-            DOT_NB(kz < nz - 1, op.cz[v], sz)
+            DOT_NB(i > 0, op.cf[v - 1].cx, -(int64_t)kp)
+            DOT_NB(i < nx - 1, cv.cx, (int64_t)kp)
+            DOT_NB(j > 0, op.cf[v - nx].cy, -(int64_t)nx * kp)
+            DOT_NB(j < op.ny - 1, cv.cy, (int64_t)nx * kp)
+            DOT_NB(kz > 0, op.cf[v - nxy].cz, -(int64_t)nxy * kp)
+            DOT_NB(kz < op.nz - 1, cv.cz, (int64_t)nxy * kp)
 #undef DOT_NB
-            st16(q + e, acc);
+            st16(qq + e, acc);
 #pragma unroll
-            for (int u = 0; u < W; ++u)
-                if (run[u]) pq[u] = eadd(pq[u], emul(pc.e[u], acc.e[u]));
+            for (int u = 0; u < W; ++u) pq[u] = eadd(pq[u], emul(pc.e[u], acc.e[u]));
         }
     }
     double2 pa[W];
@@ -637,10 +635,7 @@ template <typename T>
 static Op<T> make_op(const OpRaw& o) {
     using R = typename Elem<T>::R;
     Op<T> op;
-    op.cx = static_cast<const R*>(o.cx);
-    op.cy = static_cast<const R*>(o.cy);
-    op.cz = static_cast<const R*>(o.cz);
-    op.dre = static_cast<const R*>(o.dre);
+    op.cf = static_cast<const Cf4<R>*>(o.cf);
     op.dinv = static_cast<const T*>(o.dinv);
     op.w = (R)o.w;
     op.nx = o.nx;
