@@ -49,6 +49,7 @@ extern "C" {
 #define DOT_ECUDA      -4  /* CUDA runtime error                                 */
 #define DOT_ENOTCONV   -5  /* Krylov solve hit maxit; outputs are still written  */
 #define DOT_EBREAKDOWN -6  /* CG/COCG breakdown (zero p^T A p or rho)            */
+#define DOT_ETIMEOUT   -7  /* a bounded device-side wait ran out; results invalid */
 
 /* boundary flags */
 #define DOT_BC_ROBIN      0  /* 0.25 eta + (D/2) d eta / d xi = 0, Eq. (PDE)      */
@@ -185,6 +186,11 @@ int dot_jacobian_p(dot_ctx* ctx, double* Jp);
 int dot_get_mua(dot_ctx* ctx, double* mu);
 int dot_get_fields(dot_ctx* ctx, double* U, double* Z);
 int dot_get_stats(dot_ctx* ctx, dot_stats* stats);
+/* Stencil implementation of the block solve: tma != 0 (default) stages p through
+ * shared memory with tensor-memory-accelerator copies wherever the block allows it
+ * (FP32/complex64 recurrence, nx and ny multiples of 8, padded block width a
+ * multiple of 32); 0 always uses the direct-load kernel.  Results agree to rounding. */
+int dot_set_stencil_path(dot_ctx* ctx, int tma);
 /* Kernel timing: enable != 0 resets the counters and records CUDA events around
  * every Krylov kernel launch (on the context stream); 0 stops recording. */
 int dot_set_kernel_timing(dot_ctx* ctx, int enable);

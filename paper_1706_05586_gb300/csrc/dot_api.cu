@@ -108,6 +108,7 @@ struct dot_ctx {
     double rtol = 1e-10;
     int maxit = 0;
     double delta = 1e-3;  // reliable-update threshold of the mixed-precision recurrence
+    bool use_tma = true;  // TMA-staged stencil where the block shape allows it
 
     // block vectors: FP64 right-hand side, solution and true residual; the recurrence
     // vectors x~, r~, p, q in the inner precision
@@ -245,17 +246,19 @@ int alloc_colstate(dot_ctx* c, int kp, int max_grid, ColState* st) {
     st->n_active = misc;
     st->n_update = misc + 1;
     st->counter = reinterpret_cast<unsigned*>(misc + 4);
+    st->error = misc + 6;
     st->partA = c->partA.as<double2>();
     st->partB = c->partB.as<double>();
     return DOT_OK;
 }
 
-// Reads n_active and n_update (adjacent words) after the work queued so far.
+// Reads n_active, n_update and the kernel error word after the work queued so far.
 int read_counts(dot_ctx* c, const ColState& st, int* act, int* upd) {
-    CK(cudaMemcpyAsync(c->h_flag, st.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(c->h_flag, st.n_active, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
     *act = c->h_flag[0];
     *upd = c->h_flag[1];
+    if (c->h_flag[6] != 0) return fail(DOT_ETIMEOUT, "a bounded wait in the stencil kernel ran out");
     return DOT_OK;
 }
 
@@ -296,6 +299,9 @@ int block_solve(dot_ctx* c, int kp, std::vector<int>& iters, std::vector<int>& u
     for (DevBuf* b : {&c->xi, &c->ri, &c->pi, &c->qi}) TRY(ensure(*b, nk * ei));
     const OpRaw oi = mixed ? op32(c) : op64(c), o64 = op64(c);
     const double delta = mixed ? c->delta : 0.0;
+    TmaStencil tma;
+    const bool use_tma = c->use_tma && tma_stencil_eligible(inner, c->nx, c->ny, kp);
+    if (use_tma) CK(tma_stencil_prepare(inner, c->pi.p, c->nx, c->ny, c->nz, kp, c->num_sms, &tma));
     const int maxit = c->maxit > 0 ? c->maxit : 10 * (c->nx + c->ny + c->nz);
     CK(solve_start(inner, oi, c->b64.p, c->x64.p, c->xi.p, c->ri.p, c->pi.p, n, kp, st, c->rtol, L, c->s));
     count(c, 2);
@@ -305,8 +311,8 @@ int block_solve(dot_ctx* c, int kp, std::vector<int>& iters, std::vector<int>& u
     while (act > 0 && it < maxit + 2 * kPoll) {
         const bool first_batch = first;
         for (int m = 0; m < kPoll; ++m) {
-            CK(kry_step(inner, oi, c->xi.p, c->ri.p, c->pi.p, c->qi.p, n, kp, st, delta, maxit, !first, Lv, c->s,
-                        c->timing ? &c->tev[4 * m] : nullptr));
+            CK(kry_step(inner, oi, c->xi.p, c->ri.p, c->pi.p, c->qi.p, n, kp, st, delta, maxit, !first, Lv,
+                        use_tma ? &tma : nullptr, c->s, c->timing ? &c->tev[4 * m] : nullptr));
             count(c, first ? 2 : 3);
             first = false;
         }
@@ -529,7 +535,7 @@ int dot_create(dot_ctx** out, int device) {
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_flag, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_flag, 8 * sizeof(int));
     for (int t = 0; t < 4 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->ev[t]);
     for (int t = 0; t < 34 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->tev[t]);
     if (e != cudaSuccess) {
@@ -908,6 +914,13 @@ int dot_get_fields(dot_ctx* c, double* U, double* Z) {
 int dot_get_stats(dot_ctx* c, dot_stats* out) {
     if (!c || !out) return fail(DOT_EINVAL, "null argument");
     *out = c->stats;
+    return DOT_OK;
+}
+
+int dot_set_stencil_path(dot_ctx* c, int tma) {
+    TRY(need_ctx(c));
+    c->use_tma = tma != 0;
+    invalidate_fields(c);
     return DOT_OK;
 }
 

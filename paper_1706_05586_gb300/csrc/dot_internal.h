@@ -30,6 +30,7 @@ struct ColState {
     int* n_active;     // [1] active columns after the last finaliser
     int* n_update;     // [1] active columns waiting for an update
     unsigned* counter; // [1] arrival counter of the last-block finaliser
+    int* error;        // [1] nonzero after a bounded wait in a kernel ran out
     double2* partA;    // [grid * kp] per-block partial sums
     double* partB;     // [grid * kp]
 };
@@ -50,6 +51,19 @@ struct Launch {
     int threads;   // kp * slots
 };
 
+// TMA-staged stencil (stencil_tma.cu): tensor map over the p block and launch shape.
+struct TmaStencil {
+    alignas(64) unsigned char tmap[128];  // CUtensorMap
+    int zc = 0;                           // z planes per work item
+    int grid = 0;
+    size_t smem = 0;
+};
+bool tma_stencil_eligible(ElemKind inner, int nx, int ny, int kp);
+cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, int nx, int ny, int nz, int kp, int num_sms,
+                                TmaStencil* out);
+cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& op, const TmaStencil& t, void* q, int kp,
+                               const ColState& st, cudaStream_t s);
+
 // Launch shape of the scalar kernels (one column per thread, four blocks per SM).
 Launch krylov_launch(int64_t n, int kp, int num_sms);
 // Launch shape of the vectorised iteration kernels (W columns per thread).
@@ -66,8 +80,8 @@ cudaError_t solve_start(ElemKind inner, const OpRaw& op, const void* b64, void* 
 // x~/r~ update with convergence / refresh decisions.  ev, when not null, receives
 // four event records around the three launches.
 cudaError_t kry_step(ElemKind inner, const OpRaw& op, void* x, void* r, void* p, void* q, int64_t n, int kp,
-                     const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv, cudaStream_t s,
-                     cudaEvent_t* ev);
+                     const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv,
+                     const TmaStencil* tma, cudaStream_t s, cudaEvent_t* ev);
 // Reliable update of the paused columns: promote x~, FP64 true residual, rescale r~.
 cudaError_t solve_refresh(ElemKind inner, const OpRaw& op, const OpRaw& op64, const void* b64, void* x64, void* r64,
                           void* x, void* r, int64_t n, int kp, const ColState& st, double rtol, int maxit,

@@ -20,6 +20,7 @@
 // per-column scalar update, so no floating-point atomics are used.
 #include "dot_kernels.cuh"
 #include "dot_internal.h"
+#include "dot_reduce.cuh"
 #include "dot.h"
 
 namespace dotk {
@@ -37,132 +38,6 @@ Launch krylov_launch(int64_t n, int kp, int num_sms) {
 
 static size_t red_smem(const Launch& L, int kp) {
     return (size_t)L.slots * kp * (sizeof(double2) + sizeof(double));
-}
-
-// -------------------------------------------------------------- block reduction
-// Sum per-column values over the block's voxel slots (fixed order) and store the
-// block's partial sums.
-__device__ __forceinline__ void column_partials(double2 a, double b, int kp, int slots, int c, int slot,
-                                                double2* partA, double* partB) {
-    extern __shared__ unsigned char smem_raw[];
-    double2* sA = reinterpret_cast<double2*>(smem_raw);
-    double* sB = reinterpret_cast<double*>(sA + slots * kp);
-    sA[slot * kp + c] = a;
-    sB[slot * kp + c] = b;
-    __syncthreads();
-    if (slot == 0) {
-        double2 ta = make_double2(0.0, 0.0);
-        double tb = 0.0;
-        for (int s = 0; s < slots; ++s) {
-            ta.x += sA[s * kp + c].x;
-            ta.y += sA[s * kp + c].y;
-            tb += sB[s * kp + c];
-        }
-        if (partA) partA[(int64_t)blockIdx.x * kp + c] = ta;
-        if (partB) partB[(int64_t)blockIdx.x * kp + c] = tb;
-    }
-}
-
-// True in every thread of the last block to finish its partial sums.
-__device__ __forceinline__ bool arrive_last(unsigned* counter) {
-    __shared__ int am_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned t = atomicAdd(counter, 1u);
-        am_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    return am_last != 0;
-}
-
-// Totals of the per-block partial sums, computed by every thread of the last block:
-// tpc = blockDim / kp threads share a column, each summing a fixed strided subset of
-// the blocks with eight independent accumulators, and the subsets are combined in a
-// fixed order, so the result does not depend on scheduling.  Returns pointers to the
-// kp totals in shared memory (valid until the block exits).
-__device__ __noinline__ void block_sums(const double2* partA, const double* partB, int kp, const double2** outA,
-                                        const double** outB) {
-    extern __shared__ unsigned char smem_raw[];
-    double2* sA = reinterpret_cast<double2*>(smem_raw);
-    const int tpc = max(1, (int)blockDim.x / kp);
-    double* sB = reinterpret_cast<double*>(sA + tpc * kp);
-    const int G = gridDim.x;
-    for (int t = threadIdx.x; t < kp * tpc; t += blockDim.x) {
-        const int cc = t % kp, q = t / kp;
-        // two passes with four independent accumulators each keep the register
-        // footprint of this rarely-run code below that of the kernels' main loops
-        double2 ta = make_double2(0.0, 0.0);
-        if (partA) {
-            double2 a0 = ta, a1 = ta, a2 = ta, a3 = ta;
-            int g = q;
-            for (; g + 3 * tpc < G; g += 4 * tpc) {
-                const double2 x0 = __ldcg(&partA[(int64_t)g * kp + cc]);
-                const double2 x1 = __ldcg(&partA[(int64_t)(g + tpc) * kp + cc]);
-                const double2 x2 = __ldcg(&partA[(int64_t)(g + 2 * tpc) * kp + cc]);
-                const double2 x3 = __ldcg(&partA[(int64_t)(g + 3 * tpc) * kp + cc]);
-                a0.x += x0.x; a0.y += x0.y;
-                a1.x += x1.x; a1.y += x1.y;
-                a2.x += x2.x; a2.y += x2.y;
-                a3.x += x3.x; a3.y += x3.y;
-            }
-            for (; g < G; g += tpc) {
-                const double2 x0 = __ldcg(&partA[(int64_t)g * kp + cc]);
-                a0.x += x0.x;
-                a0.y += x0.y;
-            }
-            ta = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
-        }
-        double tb = 0.0;
-        if (partB) {
-            double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
-            int g = q;
-            for (; g + 3 * tpc < G; g += 4 * tpc) {
-                b0 += __ldcg(&partB[(int64_t)g * kp + cc]);
-                b1 += __ldcg(&partB[(int64_t)(g + tpc) * kp + cc]);
-                b2 += __ldcg(&partB[(int64_t)(g + 2 * tpc) * kp + cc]);
-                b3 += __ldcg(&partB[(int64_t)(g + 3 * tpc) * kp + cc]);
-            }
-            for (; g < G; g += tpc) b0 += __ldcg(&partB[(int64_t)g * kp + cc]);
-            tb = (b0 + b1) + (b2 + b3);
-        }
-        sA[q * kp + cc] = ta;
-        sB[q * kp + cc] = tb;
-    }
-    __syncthreads();
-    for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-        for (int q = 1; q < tpc; ++q) {
-            sA[cc].x += sA[q * kp + cc].x;
-            sA[cc].y += sA[q * kp + cc].y;
-            sB[cc] += sB[q * kp + cc];
-        }
-    }
-    __syncthreads();
-    *outA = sA;
-    *outB = sB;
-}
-
-// Column counters written by the finalisers: active columns and columns paused for
-// a reliable update.  Also re-arms the arrival counter.
-__device__ __forceinline__ void publish_counts(const ColState& st, int kp) {
-    __shared__ int na, nu;
-    if (threadIdx.x == 0) {
-        na = 0;
-        nu = 0;
-    }
-    __syncthreads();
-    for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-        if (st.active[cc]) {
-            atomicAdd(&na, 1);
-            if (st.upd[cc]) atomicAdd(&nu, 1);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        *st.n_active = na;
-        *st.n_update = nu;
-        *st.counter = 0u;
-    }
 }
 
 constexpr int kRefreshEvery = 256;
@@ -186,7 +61,7 @@ __global__ void k_start_norm(const T64* __restrict__ b, T64* __restrict__ x64, i
     if (arrive_last(st.counter)) {
         const double2* totA;
         const double* totB;
-        block_sums(nullptr, st.partB, kp, &totA, &totB);
+        block_sums(nullptr, st.partB, kp, smem_raw, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             const double2 a = totA[cc];
             const double bsum = totB[cc];
@@ -232,7 +107,7 @@ __global__ void k_start_inner(Op<T> op, const T64* __restrict__ b, T* __restrict
     if (arrive_last(st.counter)) {
         const double2* totA;
         const double* totB;
-        block_sums(st.partA, st.partB, kp, &totA, &totB);
+        block_sums(st.partA, st.partB, kp, smem_raw, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!st.active[cc]) continue;
             const double2 a = totA[cc];
@@ -358,7 +233,7 @@ __global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T
     if (arrive_last(st.counter)) {
         const double2* totA;
         const double* totB;
-        block_sums(st.partA, nullptr, kp, &totA, &totB);
+        block_sums(st.partA, nullptr, kp, smem_raw, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!running(st, cc)) continue;
             const double2 a = totA[cc];
@@ -428,7 +303,7 @@ __global__ void __launch_bounds__(256) k_xr(Op<T> op, const T* __restrict__ p, c
     if (arrive_last(st.counter)) {
         const double2* totA;
         const double* totB;
-        block_sums(st.partA, st.partB, kp, &totA, &totB);
+        block_sums(st.partA, st.partB, kp, smem_raw, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!running(st, cc)) continue;
             const double2 a = totA[cc];
@@ -538,7 +413,7 @@ __global__ void k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64
     if (arrive_last(st.counter)) {
         const double2* totA;
         const double* totB;
-        block_sums(nullptr, st.partB, kp, &totA, &totB);
+        block_sums(nullptr, st.partB, kp, smem_raw, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             const bool s2 = all ? true : (st.active[cc] != 0);
             if (!s2) continue;
@@ -596,7 +471,7 @@ __global__ void k_refresh(Op<T> op, const T64* __restrict__ r64, T* __restrict__
     if (arrive_last(st.counter)) {
         const double2* totA;
         const double* totB;
-        block_sums(st.partA, st.partB, kp, &totA, &totB);
+        block_sums(st.partA, st.partB, kp, smem_raw, &totA, &totB);
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!st.active[cc]) continue;
             const double2 a = totA[cc];
@@ -672,15 +547,20 @@ cudaError_t solve_start(ElemKind inner, const OpRaw& o, const void* b64, void* x
 }
 
 cudaError_t kry_step(ElemKind inner, const OpRaw& o, void* x, void* r, void* p, void* q, int64_t n, int kp,
-                     const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv, cudaStream_t s,
-                     cudaEvent_t* ev) {
+                     const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv,
+                     const TmaStencil* tma, cudaStream_t s, cudaEvent_t* ev) {
     DOT_DISPATCH2(inner, {
         Op<T> op = make_op<T>(o);
         const size_t sm = red_smem(Lv, kp);
         if (ev) cudaEventRecord(ev[0], s);
         if (with_p) k_p<T><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, (T*)p, n, kp, Lv.slots, st);
         if (ev) cudaEventRecord(ev[1], s);
-        k_pq<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)p, (T*)q, kp, Lv.slots, st);
+        if (tma) {
+            const cudaError_t e = tma_stencil_launch(inner, o, *tma, q, kp, st, s);
+            if (e != cudaSuccess) return e;
+        } else {
+            k_pq<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)p, (T*)q, kp, Lv.slots, st);
+        }
         if (ev) cudaEventRecord(ev[2], s);
         k_xr<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)p, (const T*)q, (T*)x, (T*)r, n, kp, Lv.slots, st,
                                                  delta, maxit);

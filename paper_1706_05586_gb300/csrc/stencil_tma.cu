@@ -1,0 +1,323 @@
+// TMA-staged stencil q = A p with the per-column dot products p^T q (sm_103a).
+//
+// The 7-point operator of Sec. 2 (Eq. (PDE), Eq. (Eq:compmeas)) is applied to a
+// block of right-hand-side columns.  A CTA owns a tile of 8 x 8 cells x 32 columns
+// and marches it through a range of z planes.  Each plane of the tile, with a
+// one-cell halo in x and y, is brought into shared memory by one
+// cp.async.bulk.tensor load (4-D tensor map over [z][y][x][column]), four planes
+// deep, so every element of p crosses L2 once per plane instead of once per
+// neighbour; the z neighbours are the adjacent planes of the ring.  Out-of-range
+// halo cells are zero-filled by the copy engine (their coefficients are zero or
+// skipped).  A warp owns one tile row and a lane one column, so shared-memory reads
+// and global stores are 256-byte (complex64) or 128-byte (FP32) rows.
+//
+// Every wait on an mbarrier is bounded by a clock budget; on expiry the CTA records
+// an error code, drains its outstanding copies (again bounded) and stops issuing work.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "dot.h"
+#include "dot_kernels.cuh"
+#include "dot_internal.h"
+#include "dot_reduce.cuh"
+
+namespace dotk {
+
+namespace {
+
+constexpr int KC = 32;               // columns per tile
+constexpr int TX = 8, TY = 8;        // cells per tile
+constexpr int HX = TX + 2, HY = TY + 2;
+constexpr int NBUF = 4;              // planes in flight
+constexpr int THREADS = 32 * TY;     // warp w <-> tile row y = w
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the given phase parity; false if the budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+// One plane of the tile: box {KC, HX, HY, 1} at (c0, i0 - 1, j0 - 1, z).
+__device__ __forceinline__ void tma_plane(const CUtensorMap* tm, void* dst, uint64_t* bar, int c0, int x, int y,
+                                          int z, uint32_t bytes) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, bytes);
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace
+
+// Shared memory: NBUF plane buffers, NBUF mbarriers, per-warp partials, per-CTA
+// column accumulators (kp), then the finaliser scratch reuses the plane buffers.
+template <typename T>
+__global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ CUtensorMap tm, Op<T> op,
+                                                       T* __restrict__ q, int kp, int zc_len, ColState st) {
+    using R = typename Elem<T>::R;
+    constexpr int PLANE = KC * HX * HY;  // elements
+    // plane buffers start on a 128-byte boundary (the copy engine's shared-memory alignment)
+    unsigned char* base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    T* buf = reinterpret_cast<T*>(base);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)NBUF * PLANE * sizeof(T));
+    double2* wsum = reinterpret_cast<double2*>(bar + NBUF);
+    double2* acc = wsum + TY * 32;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nx = op.nx, ny = op.ny, nz = op.nz, nxy = nx * ny;
+    const int tiles_x = nx / TX, tiles_y = ny / TY, tiles_c = kp / KC;
+    const int zchunks = (nz + zc_len - 1) / zc_len;
+    const int nitems = tiles_x * tiles_y * tiles_c * zchunks;
+    const uint32_t plane_bytes = PLANE * sizeof(T);
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init(&bar[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int c = threadIdx.x; c < kp; c += blockDim.x) acc[c] = make_double2(0.0, 0.0);
+    __syncthreads();
+
+    uint32_t parity = 0;    // bit b: parity of the next phase of buffer b
+    uint32_t pending = 0;   // bit b: a copy into buffer b has been issued and not waited for
+    bool failed = false;
+
+    for (int item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
+        int rem = item;
+        const int txi = rem % tiles_x;
+        rem /= tiles_x;
+        const int tyi = rem % tiles_y;
+        rem /= tiles_y;
+        const int cci = rem % tiles_c;
+        const int zci = rem / tiles_c;
+        const int i0 = txi * TX, j0 = tyi * TY, c0 = cci * KC;
+        const int z0 = zci * zc_len, z1 = min(z0 + zc_len, nz);
+        const int c = c0 + lane;
+        const bool run = st.active[c] && !st.upd[c];
+        if (!__syncthreads_or(run)) continue;
+
+        // planes z0-1 .. z1 go to buffers (z - z0 + 1) mod NBUF
+        auto slot = [&](int z) { return (z - z0 + 1) & (NBUF - 1); };
+        if (threadIdx.x == 0) {
+            for (int z = z0 - 1; z <= min(z0 + 1, z1); ++z)
+                tma_plane(&tm, buf + (size_t)slot(z) * PLANE, &bar[slot(z)], c0, i0 - 1, j0 - 1, z, plane_bytes);
+        }
+        for (int z = z0 - 1; z <= min(z0 + 1, z1); ++z) pending |= 1u << slot(z);
+        bool ok = true;
+        for (int z = z0 - 1; z <= z0 && ok; ++z) {
+            const int b = slot(z);
+            ok = mbar_wait(&bar[b], (parity >> b) & 1u);
+            if (ok) {
+                parity ^= 1u << b;
+                pending &= ~(1u << b);
+            }
+        }
+        failed = __syncthreads_or(!ok);
+        T pq = ezero<T>();
+        for (int k = z0; k < z1 && !failed; ++k) {
+            if (k + 2 <= z1) {
+                const int b = slot(k + 2);
+                if (threadIdx.x == 0)
+                    tma_plane(&tm, buf + (size_t)b * PLANE, &bar[b], c0, i0 - 1, j0 - 1, k + 2, plane_bytes);
+                pending |= 1u << b;
+            }
+            {
+                const int b = slot(k + 1);
+                ok = mbar_wait(&bar[b], (parity >> b) & 1u);
+                if (ok) {
+                    parity ^= 1u << b;
+                    pending &= ~(1u << b);
+                }
+            }
+            failed = __syncthreads_or(!ok);
+            if (failed) break;
+            const T* pm = buf + (size_t)slot(k - 1) * PLANE;
+            const T* pc = buf + (size_t)slot(k) * PLANE;
+            const T* pn = buf + (size_t)slot(k + 1) * PLANE;
+            const int j = j0 + warp;
+            const int row = (warp + 1) * HX * KC;
+#pragma unroll 2
+            for (int xi = 0; xi < TX; ++xi) {
+                const int i = i0 + xi;
+                const int v = i + nx * (j + ny * k);
+                const int o = row + (xi + 1) * KC + lane;
+                const Cf4<R> cv = op.cf[v];
+                const T xc = pc[o];
+                T a = escale(cv.dre, xc);
+                if (Elem<T>::cplx) a = eadd(a, emul_i(op.w, xc));
+                if (i > 0) a = esub(a, escale(op.cf[v - 1].cx, pc[o - KC]));
+                a = esub(a, escale(cv.cx, pc[o + KC]));
+                if (j > 0) a = esub(a, escale(op.cf[v - nx].cy, pc[o - HX * KC]));
+                a = esub(a, escale(cv.cy, pc[o + HX * KC]));
+                if (k > 0) a = esub(a, escale(op.cf[v - nxy].cz, pm[o]));
+                a = esub(a, escale(cv.cz, pn[o]));
+                q[(int64_t)v * kp + c] = a;
+                pq = eadd(pq, emul(xc, a));
+            }
+            __syncthreads();  // plane k-1's buffer is refilled in the next iteration
+        }
+        if (failed) break;
+        // fold this item's per-lane sums into the CTA's column accumulators in warp order
+        wsum[warp * 32 + lane] = ewide(pq);
+        __syncthreads();
+        if (warp == 0) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int w = 0; w < TY; ++w) {
+                s.x += wsum[w * 32 + lane].x;
+                s.y += wsum[w * 32 + lane].y;
+            }
+            acc[c].x += s.x;
+            acc[c].y += s.y;
+        }
+        __syncthreads();
+    }
+
+    if (failed) {
+        if (threadIdx.x == 0) atomicExch(st.error, 1);
+        // drain this CTA's copies still in flight before shared memory is released
+        for (int b = 0; b < NBUF; ++b)
+            if (pending & (1u << b)) mbar_wait(&bar[b], (parity >> b) & 1u);
+        __syncthreads();
+    }
+    for (int c = threadIdx.x; c < kp; c += blockDim.x) st.partA[(int64_t)blockIdx.x * kp + c] = acc[c];
+    if (arrive_last(st.counter)) {
+        const double2* totA;
+        const double* totB;
+        block_sums(st.partA, nullptr, kp, base, &totA, &totB);
+        for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
+            if (!(st.active[cc] && !st.upd[cc])) continue;
+            const double2 a = totA[cc];
+            if (!zfinite(a) || (a.x == 0.0 && a.y == 0.0)) {
+                st.status[cc] = DOT_EBREAKDOWN;
+                st.active[cc] = 0;
+                continue;
+            }
+            st.alpha[cc] = zdiv(st.rho[cc], a);
+        }
+        __syncthreads();
+        publish_counts(st, kp);
+    }
+}
+
+// ---------------------------------------------------------------------- host
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool tma_stencil_eligible(ElemKind inner, int nx, int ny, int kp) {
+    return (inner == EK_C64 || inner == EK_F32) && nx % TX == 0 && ny % TY == 0 && kp % KC == 0 && kp <= 1024 &&
+           encode_fn() != nullptr;
+}
+
+static size_t tma_smem(size_t es, int kp) {
+    return 128 + (size_t)NBUF * KC * HX * HY * es + NBUF * sizeof(uint64_t) + (size_t)TY * 32 * sizeof(double2) +
+           (size_t)kp * sizeof(double2);
+}
+
+cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, int nx, int ny, int nz, int kp, int num_sms,
+                                TmaStencil* out) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const size_t es = inner == EK_C64 ? 8 : 4;
+    const cuuint64_t dims[4] = {(cuuint64_t)kp, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[3] = {(cuuint64_t)kp * es, (cuuint64_t)kp * nx * es, (cuuint64_t)kp * nx * ny * es};
+    const cuuint32_t box[4] = {KC, HX, HY, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = enc(reinterpret_cast<CUtensorMap*>(out->tmap), inner == EK_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64
+                                                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                           4, const_cast<void*>(p), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    // z-chunk length: balance whole waves of items against the two halo planes per chunk
+    const int tiles = (nx / TX) * (ny / TY) * (kp / KC);
+    const int grid_cap = 2 * num_sms;
+    int best = nz;
+    double best_cost = 1e300;
+    for (int zc : {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, nz}) {
+        if (zc > nz || zc < 1) continue;
+        const long items = (long)tiles * ((nz + zc - 1) / zc);
+        const long grid = items < grid_cap ? items : grid_cap;
+        const double waves = (double)((items + grid - 1) / grid);
+        const double cost = waves * (zc + 2);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = zc;
+        }
+    }
+    out->zc = best;
+    const long items = (long)tiles * ((nz + best - 1) / best);
+    out->grid = (int)(items < grid_cap ? items : grid_cap);
+    out->smem = tma_smem(es, kp);
+    cudaError_t e;
+    if (inner == EK_C64)
+        e = cudaFuncSetAttribute(k_pq_tma<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
+    else
+        e = cudaFuncSetAttribute(k_pq_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
+    return e;
+}
+
+cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil& t, void* q, int kp,
+                               const ColState& st, cudaStream_t s) {
+    const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(t.tmap);
+    if (inner == EK_C64) {
+        Op<float2> op;
+        op.cf = static_cast<const Cf4<float>*>(o.cf);
+        op.dinv = static_cast<const float2*>(o.dinv);
+        op.w = (float)o.w;
+        op.nx = o.nx;
+        op.ny = o.ny;
+        op.nz = o.nz;
+        k_pq_tma<float2><<<t.grid, THREADS, t.smem, s>>>(*tm, op, (float2*)q, kp, t.zc, st);
+    } else if (inner == EK_F32) {
+        Op<float> op;
+        op.cf = static_cast<const Cf4<float>*>(o.cf);
+        op.dinv = static_cast<const float*>(o.dinv);
+        op.w = 0.f;
+        op.nx = o.nx;
+        op.ny = o.ny;
+        op.nz = o.nz;
+        k_pq_tma<float><<<t.grid, THREADS, t.smem, s>>>(*tm, op, (float*)q, kp, t.zc, st);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace dotk

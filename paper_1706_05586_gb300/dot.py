@@ -21,6 +21,7 @@ DOT_ENOMEM = -3
 DOT_ECUDA = -4
 DOT_ENOTCONV = -5
 DOT_EBREAKDOWN = -6
+DOT_ETIMEOUT = -7
 BC_ROBIN = 0
 BC_DIRICHLET = 1
 PREC_FP64 = 0
@@ -57,6 +58,7 @@ SIGNATURES = {
     "dot_get_stats": [C.c_void_p, C.c_void_p],
     "dot_apply": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "dot_set_kernel_timing": [C.c_void_p, C.c_int],
+    "dot_set_stencil_path": [C.c_void_p, C.c_int],
     "dot_get_kernel_timing": [C.c_void_p, C.c_void_p],
 }
 _RESTYPE = {"dot_last_error": C.c_char_p}
@@ -266,6 +268,10 @@ def dot_get_stats(ctx) -> dict:
     s = DotStats()
     _check(load().dot_get_stats(ctx, C.byref(s)))
     return s.as_dict()
+
+
+def dot_set_stencil_path(ctx, tma):
+    return _check(load().dot_set_stencil_path(ctx, int(bool(tma))))
 
 
 def dot_set_kernel_timing(ctx, enable):

@@ -39,6 +39,11 @@ CASES = {
                                             seed_index=63),
     # the 32x32x16 workload (16,384 cells, 27 RBFs, 2 + 2 Rademacher columns)
     "dot32x32x16": synth.WORKLOADS["dot32x32x16"],
+    # a block of 16 + 16 columns on 8-aligned x, y: the mixed path takes the TMA-staged stencil
+    "cplx_24x16x10_k32": synth.small_workload(24, 16, 10, 0.3, omega_nu=0.4, src_grid=(4, 4), det_grid=(4, 4),
+                                              ls=16, ld=16, m0=5, sampling="gaussian", seed_index=65),
+    "real_16x16x9_k32": synth.small_workload(16, 16, 9, 0.3, src_grid=(4, 4), det_grid=(4, 4), ls=16, ld=16,
+                                             m0=4, sampling="gaussian", seed_index=66),
     # the 100 MHz frequency on a 24x20x12 grid
     "cplx_24x20x12_100MHz": synth.small_workload(24, 20, 12, 0.25, omega_nu=synth.OMEGA_NU_100MHZ, src_grid=(3, 3),
                                                  det_grid=(3, 3), ls=4, ld=4, m0=8, sampling="gaussian",
@@ -238,3 +243,21 @@ def test_forward_model_all_sources(name, ctx):
     f, _ = D.dot_misfit(ctx)
     out = orc.evaluate(pb.D, mu, pb.grid, pb.wl.bc, pb.wl.omega_nu, pb.Bd, pb.Cd, pb.M, pb.inp.W, pb.inp.V)
     assert misfit_err(f, out) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["cplx_24x16x10_k32", "real_16x16x9_k32"])
+def test_tma_stencil_matches_direct_load_kernel(name, ctx):
+    """The TMA-staged stencil and the direct-load stencil give the same solve to rounding."""
+    pb, ref = _case(name)
+    out = {}
+    for tma in (1, 0):
+        configure(ctx, pb, p=pb.inp.p0, prec=D.PREC_MIXED, rtol=1e-13)
+        D.dot_set_stencil_path(ctx, tma)
+        f, g, rc = D.dot_gradient(ctx, pb.wl.np_)
+        assert rc == D.DOT_OK
+        out[tma] = (f, g, D.dot_get_stats(ctx)["iters_max"])
+    D.dot_set_stencil_path(ctx, 1)
+    assert abs(out[1][0] - out[0][0]) <= 1e-10 * abs(out[0][0])
+    assert rel(out[1][1], out[0][1]) <= 1e-9
+    assert abs(out[1][2] - out[0][2]) <= 3
+    assert misfit_err(out[1][0], ref) <= 1e-8
