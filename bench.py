@@ -128,7 +128,9 @@ def measured_peaks():
 
 
 def ncu_traffic(kernel_key, workload):
-    """dram bytes per launch of a kernel from a committed ncu summary, if any."""
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or None when there is
+    none or the kernel's source has changed since the counters were taken."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -136,8 +138,11 @@ def ncu_traffic(kernel_key, workload):
         if ln.startswith("#") or not ln.strip():
             continue
         parts = ln.split()
-        if len(parts) >= 4 and parts[0] == kernel_key and parts[1] == workload:
-            return parts
+        if len(parts) >= 5 and parts[0] == kernel_key and parts[1] == workload:
+            src = os.path.join(ROOT, parts[2])
+            if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != parts[3]:
+                return None
+            return float(parts[4])
     return None
 
 
@@ -248,13 +253,7 @@ def run_ours(args):
     kd = kt[dom]
     achieved = kd["bytes"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else 0.0
     per_launch_bytes = kd["bytes"] / max(kd["launches"], 1)
-    trow = ncu_traffic(dom, args.workload)
-    traffic = None
-    if trow is not None:
-        try:
-            traffic = float(trow[3])
-        except ValueError:
-            traffic = None
+    traffic = ncu_traffic(dom, args.workload)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": kd["ms"] / max(kd["launches"], 1),
