@@ -201,6 +201,34 @@ int dot_get_kernel_timing(dot_ctx* ctx, dot_kernel_timing* out);
  * The 7-point stencil of the block solve, exposed for testing. */
 int dot_apply(dot_ctx* ctx, int k, const double* x, double* y);
 
+/* Allocation-free restriction and misfit (this library's addition; the paper has
+ * no counterpart).  For callers that cannot let the library allocate device memory:
+ * a latency-critical loop that must not stall on cudaMalloc / cudaFree (which can
+ * synchronize the device), or a process whose device memory is owned entirely by
+ * another allocator.  Computes, from fields already on the device,
+ *   T = C^T U (n_d x l_s),  S = V^T T (l_d x l_s),  R_s = S - P,  f = ||R_s||_F^2,
+ * the restriction and misfit of Eq. (EsTResidual) / Theorem 1, with the same kernels
+ * as dot_misfit.  All pointers are DEVICE pointers on the current device; the work
+ * is queued on `stream` (a cudaStream_t, NULL for the default stream) and nothing
+ * is synchronized.
+ *   X: block of fields over n cells, element (v, c) at v * kp + c (double, or
+ *      interleaved complex when is_complex), kp >= ls, columns 0..ls-1 the forward
+ *      fields U (further columns, e.g. the adjoint fields, are not read);
+ *   colptrC (nd + 1, int64), rowsC, valsC: detectors C as CSC;  V: nd x ld column-major;
+ *   P: l_d x l_s interleaved complex V^T M W, or NULL for no data (R_s = S);
+ *   S, Rs: l_d x l_s interleaved complex outputs;  f: one double.
+ * The only scratch, T, is a fixed device array of DOT_NOALLOC_MAX_T complex entries
+ * (1 MiB) that every GPU loading the library holds until the process exits;
+ * nd * ls above that limit is rejected with DOT_EINVAL.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress), so make it before any
+ * stream capture.  All calls share the array, which keeps the last call's contents
+ * (each call overwrites every entry it reads); calls that overlap on the GPU race. */
+#define DOT_NOALLOC_MAX_T 65536
+int dot_restrict_misfit_noalloc(const double* X, int64_t n, int kp, int ls, int ld, const int64_t* colptrC,
+                                const int32_t* rowsC, const double* valsC, int nd, const double* V,
+                                const double* P, int is_complex, double* S, double* Rs, double* f,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

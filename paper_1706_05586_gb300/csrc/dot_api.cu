@@ -68,6 +68,8 @@ void release(DevBuf& b) {
 
 }  // namespace
 
+int dotk::record_error(int code, const std::string& msg) { return fail(code, msg); }
+
 struct dot_ctx {
     int device = 0;
     int num_sms = 152;

@@ -5,7 +5,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace dotk {
+
+// Sets the calling thread's dot_last_error() message; returns code.
+int record_error(int code, const std::string& msg);
 
 // Per-column Krylov state of one block solve (device pointers, length kp unless noted).
 // The recurrence runs on r~ = r / scale; the FP64 solution and true residual are separate.

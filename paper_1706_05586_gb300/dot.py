@@ -59,6 +59,9 @@ SIGNATURES = {
     "dot_apply": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "dot_set_kernel_timing": [C.c_void_p, C.c_int],
     "dot_set_stencil_path": [C.c_void_p, C.c_int],
+    "dot_restrict_misfit_noalloc": [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p],
     "dot_get_kernel_timing": [C.c_void_p, C.c_void_p],
 }
 _RESTYPE = {"dot_last_error": C.c_char_p}
@@ -291,6 +294,15 @@ def dot_apply(ctx, X, cplx):
     Y = np.zeros_like(X, order="F")
     _check(load().dot_apply(ctx, X.shape[1], _ptr(X), _ptr(Y)))
     return Y
+
+
+def dot_restrict_misfit_noalloc(X, n, kp, ls, ld, colptrC, rowsC, valsC, nd, V, P, is_complex, S, Rs, f,
+                                stream=None):
+    """Allocation-free restriction and misfit; every array argument is a device pointer (int)."""
+    vp = lambda x: None if x is None else C.c_void_p(x)
+    return _check(load().dot_restrict_misfit_noalloc(vp(X), n, kp, ls, ld, vp(colptrC), vp(rowsC), vp(valsC), nd,
+                                                     vp(V), vp(P), int(bool(is_complex)), vp(S), vp(Rs), vp(f),
+                                                     vp(stream)))
 
 
 class Context:
