@@ -58,6 +58,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, device="cpu"):
+    """Maximum of a per-rank float over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds_per_rank, world_size, device="cpu"):
+    """Units processed by all ranks over the slowest rank's time (replicas: weak scaling)."""
+    return units_per_rank * world_size / max_over_ranks(seconds_per_rank, device)
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -238,13 +254,9 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     kt = D.dot_get_kernel_timing(ctx)
     launches = D.dot_get_stats(ctx)["kernel_launches"] - launches0
-    ms_max = ms
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = args.steps * ws / (ms_max / 1e3)
+    dev = f"cuda:{local}"
+    ms_max = max_over_ranks(ms, dev)
+    value = whole_job_rate(args.steps, ms / 1e3, ws, dev)
     f_last, g_last = f, g
 
     # dominant Krylov kernel against the HBM roofline
@@ -332,13 +344,8 @@ def run_ours(args):
             D.dot_gradient(ctx, wl.np_)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([te], dtype=torch.float64, device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        out["e2e"] = {"value": round(args.steps * ws / te, 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                      "d2h_bytes_per_step": int(d2h)}
+        out["e2e"] = {"value": round(whole_job_rate(args.steps, te, ws, dev), 4), "unit": UNIT,
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, inp, log)
