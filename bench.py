@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--api", choices=("abi", "autograd"), default="abi",
+                    help="abi: dot_set_pals_dev + dot_gradient per step; autograd: forward and backward of "
+                         "the torch.autograd.Function per step")
     return ap.parse_args()
 
 
@@ -217,9 +220,19 @@ def run_ours(args):
     pals = (synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
     m0 = wl.m0
 
-    def step(k):
-        D.dot_set_pals_dev(ctx, m0, p_dev[k].data_ptr(), *pals)
-        return D.dot_gradient(ctx, wl.np_)
+    if args.api == "autograd":
+        from paper_1706_05586_gb300.autograd import PalsConstants, misfit
+        consts = PalsConstants(*pals)
+
+        def step(k):
+            p = p_dev[k].detach().clone().requires_grad_(True)
+            f = misfit(p, ctx, consts)
+            f.backward()
+            return float(f.item()), p.grad.detach().cpu().numpy(), 0
+    else:
+        def step(k):
+            D.dot_set_pals_dev(ctx, m0, p_dev[k].data_ptr(), *pals)
+            return D.dot_gradient(ctx, wl.np_)
 
     for k in range(args.warmup):
         f, g, _ = step(k)
@@ -287,7 +300,7 @@ def run_ours(args):
                       "krylov_iters_per_step": [it[0] for it in iters], "outer_steps": [it[1] for it in iters],
                       "relres_max": max(it[2] for it in iters),
                       "l2": "inputs larger than L2 (each Krylov block vector >= 512 MiB)",
-                      "parallelism": f"replicas x{ws}"},
+                      "parallelism": f"replicas x{ws}", "api": args.api},
            "clocks": clk, "gpu_launches": int(launches), "roofline": roofline}
 
     # plain FP64 GPU path at the last p: its throughput at the same stopping rule, and a

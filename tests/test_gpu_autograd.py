@@ -1,0 +1,92 @@
+"""The misfit as a torch.autograd.Function: gradient against the FP64 oracle and
+against central differences of the library's own misfit, in checkpoint and recompute
+modes, plus a forward/backward at the 128^3 workload (2,097,152 cells, 1,000 RBFs,
+5,000 parameters) checked along a random direction."""
+import numpy as np
+import pytest
+
+from paper_1706_05586_gb300 import dot as D
+from paper_1706_05586_gb300 import synth
+from tests import problem
+from tests.gpu_setup import configure, grad_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _consts(wl):
+    from paper_1706_05586_gb300.autograd import PalsConstants
+    return PalsConstants(synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+@pytest.mark.parametrize("device", ["cuda", "cpu"])
+def test_autograd_matches_oracle(recompute, device):
+    from paper_1706_05586_gb300.autograd import misfit
+    wl = synth.small_workload(11, 6, 7, 0.35, omega_nu=0.3, src_grid=(3, 1), det_grid=(2, 2), ls=3, ld=2, m0=5,
+                              sampling="gaussian", seed_index=62)
+    pb = problem.build(wl)
+    ref = pb.evaluate(pb.inp.p0)
+    h = D.dot_create(0)
+    try:
+        configure(h, pb, p=pb.inp.p0, prec=D.PREC_MIXED, rtol=1e-13)
+        p = torch.tensor(pb.inp.p0, dtype=torch.float64, device=device, requires_grad=True)
+        f = misfit(p, h, _consts(wl), recompute=recompute)
+        (3.0 * f).backward()
+        assert abs(f.item() - ref["f"]) <= 1e-8 * ref["f"]
+        g = p.grad.cpu().numpy() / 3.0
+        assert grad_err(g, ref["g_p"], ref["J_p"], ref["R_s"], ref["S"]) <= 1e-8
+    finally:
+        D.dot_destroy(h)
+
+
+def test_backward_after_a_second_forward_uses_its_own_point():
+    from paper_1706_05586_gb300.autograd import misfit
+    wl = synth.small_workload(9, 7, 5, 0.4, src_grid=(2, 2), det_grid=(2, 1), ls=2, ld=1, m0=4, seed_index=61)
+    pb = problem.build(wl)
+    ref0 = pb.evaluate(pb.inp.p0)
+    h = D.dot_create(0)
+    try:
+        configure(h, pb, p=pb.inp.p0, prec=D.PREC_FP64, rtol=1e-14)
+        p0 = torch.tensor(pb.inp.p0, dtype=torch.float64, requires_grad=True)
+        p1 = torch.tensor(pb.inp.p_true, dtype=torch.float64, requires_grad=True)
+        f0 = misfit(p0, h, _consts(wl))
+        f1 = misfit(p1, h, _consts(wl))
+        f0.backward()
+        assert grad_err(p0.grad.numpy(), ref0["g_p"], ref0["J_p"], ref0["R_s"], ref0["S"]) <= 1e-10
+        f1.backward()
+        assert np.all(np.isfinite(p1.grad.numpy()))
+    finally:
+        D.dot_destroy(h)
+
+
+def test_autograd_128cubed_directional_difference():
+    from paper_1706_05586_gb300.autograd import misfit
+    wl = synth.WORKLOADS["dot128x128x128"]
+    inp = synth.draw(wl)
+    h = D.dot_create(0)
+    try:
+        D.dot_set_grid(h, wl.nx, wl.ny, wl.nz, wl.h, wl.bc)
+        D.dot_set_omega(h, wl.omega_nu)
+        D.dot_set_diffusion(h, np.full(wl.n, 1.0 / 30.0))
+        D.dot_set_pals(h, inp.p_true, synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
+        D.dot_set_diffusion(h, synth.diffusion_from_mua(D.dot_get_mua(h, wl.n)))
+        D.dot_set_sources(h, inp.B)
+        D.dot_set_detectors(h, inp.C)
+        rng = np.random.default_rng(4)
+        D.dot_set_data(h, 1e-6 * rng.standard_normal((wl.nd, wl.ns)))
+        D.dot_set_sampling(h, inp.W, inp.V)
+        D.dot_set_solver(h, D.PREC_MIXED, 1e-12, 0)
+        p = torch.tensor(inp.p0, dtype=torch.float64, device="cuda", requires_grad=True)
+        f = misfit(p, h, _consts(wl))
+        f.backward()
+        g = p.grad.cpu().numpy()
+        d = rng.standard_normal(wl.np_)
+        d[1::5] = 0.0
+        d /= np.linalg.norm(d)
+        eps = 1e-3
+        fp = misfit(p.detach() + eps * torch.tensor(d, device="cuda"), h, _consts(wl)).item()
+        fm = misfit(p.detach() - eps * torch.tensor(d, device="cuda"), h, _consts(wl)).item()
+        assert abs((fp - fm) / (2 * eps) - g @ d) <= 1e-4 * np.linalg.norm(g)
+    finally:
+        D.dot_destroy(h)
