@@ -377,3 +377,73 @@ def evaluate(D, mu, grid, bc, omega_nu, B, C, M, W, V, dmu=None):
         out["g_p"] = misfit_gradient(out["R_s"], Jp)
     out["Uf"], out["Zf"] = Uf, Zf
     return out
+
+
+# --------------------------------------------- optimized sources and detectors (Sec. 3.2)
+
+def _real_stack(J3):
+    """A complex tensor enters ||(W^T (x) V^T) J||_F with real W, V through its real and
+    imaginary parts, which act as separate parameter columns."""
+    J3 = np.asarray(J3)
+    if np.iscomplexobj(J3):
+        return np.concatenate([J3.real, J3.imag], axis=2)
+    return J3
+
+
+def _leading_left(Mat, q):
+    """The q leading left singular vectors of a real matrix (numpy SVD)."""
+    U, _, _ = np.linalg.svd(Mat, full_matrices=False)
+    return U[:, :q]
+
+
+def unfold_lateral(J3):
+    """J~ = [J_{:,1,:} J_{:,2,:} ... J_{:,n_s,:}] (n_d x n_s n_p), Eq. (Jtilde)."""
+    nd, ns, npar = J3.shape
+    return np.concatenate([J3[:, j, :] for j in range(ns)], axis=1)
+
+
+def contract_detectors(J3, Vt):
+    """K~ = [K_1 ... K_qd] with (K_l)_{jk} = sum_m (v_l)_m J_{mjk} (n_s x n_p q_d), Eq. (Ktilde)."""
+    return np.concatenate([np.einsum("m,mjk->jk", Vt[:, l], J3) for l in range(Vt.shape[1])], axis=1)
+
+
+def contract_sources(J3, Wt):
+    """L~ = [L_1 ... L_qs] with (L_l)_{ik} = sum_m (w_l)_m J_{imk} (n_d x n_p q_s), Eq. (Ltilde)."""
+    return np.concatenate([np.einsum("m,imk->ik", Wt[:, l], J3) for l in range(Wt.shape[1])], axis=1)
+
+
+def optimized_sources_detectors(J3, qs, qd, maxit=100, tol=1e-10):
+    """Algorithm 1 (Sec. 3.3): Tucker2 alternating iteration for isometric W^, V^ maximizing
+    ||(W^T (x) V^T) J||_F^2 (Eq. (maxprob)).
+
+    Start from the q_d leading left singular vectors of J~; then alternate W~ from K~ and
+    V~ from L~ until the change of the projectors W~W~^T, V~V~^T is below tol (reading:
+    the paper leaves the test open) or maxit sweeps.  Returns (W^, V^, sweeps).
+    """
+    J = _real_stack(J3)
+    Vt = _leading_left(unfold_lateral(J), qd)
+    Wt = None
+    for it in range(1, maxit + 1):
+        W_new = _leading_left(contract_detectors(J, Vt), qs)
+        V_new = _leading_left(contract_sources(J, W_new), qd)
+        change = np.linalg.norm(V_new @ V_new.T - Vt @ Vt.T)
+        if Wt is not None:
+            change += np.linalg.norm(W_new @ W_new.T - Wt @ Wt.T)
+        Wt, Vt = W_new, V_new
+        if it > 1 and change < tol:
+            return Wt, Vt, it
+    return Wt, Vt, maxit
+
+
+def sampled_jacobian_norm2(J3, W, V):
+    """||(W^T (x) V^T) J||_F^2 (Eq. (maxprob)), complex entries counted as |.|^2."""
+    out = np.einsum("ml,jq,mjk->lqk", V, W, np.asarray(J3))
+    return float(np.sum(np.abs(out) ** 2))
+
+
+def complement_sampling(What, Ytil):
+    """W = [W^, W_c Y] of Eq. (newW) with W_c Y read as (I - W^ W^T) Y~: Y~ has n rows and
+    i.i.d. zero-mean, covariance-(ell - q)^{-1} entries, so W_c Y has covariance I - W^W^T
+    for any orthonormal basis W_c of the complement (Theorem 2 needs only that)."""
+    P = np.eye(What.shape[0]) - What @ What.T
+    return np.concatenate([What, P @ Ytil], axis=1)
