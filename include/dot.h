@@ -179,6 +179,26 @@ int dot_jacobian_mua(dot_ctx* ctx, double* J);
  * interleaved when omega != 0).  Needs dot_set_pals. */
 int dot_jacobian_p(dot_ctx* ctx, double* Jp);
 
+/* Optimized simultaneous sources and detectors (Sec. 3.2, Algorithm 1) completed by
+ * random ones in the complementary subspace (Eqs. (newW), (newV), Theorem 2), at the
+ * current PaLS parameters.  Solves every physical source and detector once
+ * (ns + nd <= 1024 columns), forms the Jacobian tensor J_ijk of Eq. (Jtensor), and
+ * runs the Tucker2 alternating iteration: q_d leading left singular vectors of
+ * J~ = [J_{:,1,:} ... J_{:,ns,:}], then alternately W~ from K~ and V~ from L~ until the
+ * projectors change by less than tol or after maxit sweeps.  The outputs are
+ *   W = [W^, (I - W^ W^T) Ytil]  (ns x ls, column-major),  V = [V^, (I - V^ V^T) Ztil]
+ * (nd x ld): Ytil (ns x (ls - qs)) and Ztil (nd x (ld - qd)) are the caller's random
+ * draws, already scaled by (l - q)^{-1/2}; projecting them onto the complement gives the
+ * covariance I - W^ W^T of W_c Y for any basis W_c.  Complex J (omega != 0) enters
+ * through its real and imaginary parts.  1 <= qs, qd <= 8.  sweeps and objective
+ * (||(W^T (x) V^T) J||_F^2) may be NULL.  Does not change the context's sampling. */
+int dot_optimized_sampling(dot_ctx* ctx, int qs, int qd, int maxit, double tol, int ls, const double* Ytil,
+                           int ld, const double* Ztil, double* W, double* V, int* sweeps, double* objective);
+/* Host helper used by dot_optimized_sampling: eigen-decomposition of a symmetric
+ * n x n column-major matrix A (Householder tridiagonalisation, implicit QL);
+ * eigenvalues ascending in evals (n), eigenvectors in the columns of evecs (n x n). */
+int dot_symeig(int n, const double* A, double* evals, double* evecs);
+
 /* Inspection.  dot_get_mua: the absorption field in use (N doubles).
  * dot_get_fields: forward fields U (N x ls) and adjoint fields Z (N x ld),
  * column-major (complex interleaved when omega != 0); either pointer may be NULL.

@@ -858,6 +858,74 @@ int dot_forward_model(dot_ctx* c, double* M) {
     return DOT_OK;
 }
 
+int dot_optimized_sampling(dot_ctx* c, int qs, int qd, int maxit, double tol, int ls, const double* Ytil, int ld,
+                           const double* Ztil, double* W, double* V, int* sweeps, double* objective) {
+    TRY(need_grid(c));
+    if (c->mu_mode != 2) return fail(DOT_ESTATE, "dot_optimized_sampling needs dot_set_pals");
+    if (c->ns == 0 || c->nd == 0) return fail(DOT_ESTATE, "set sources and detectors first");
+    if (qs < 1 || qd < 1 || qs > 8 || qd > 8 || qs > c->ns || qd > c->nd || ls < qs || ld < qd)
+        return fail(DOT_EINVAL, "need 1 <= q <= 8, q <= n and q <= l for sources and detectors");
+    if (c->ns + c->nd > 1024) return fail(DOT_EINVAL, "ns + nd exceeds 1024");
+    if (!W || !V || (ls > qs && !Ytil) || (ld > qd && !Ztil)) return fail(DOT_EINVAL, "null array argument");
+    if (maxit < 1 || !(tol > 0.0)) return fail(DOT_EINVAL, "maxit must be positive and tol > 0");
+    TRY(ensure_coefficients(c));
+    const bool cx_ = cplx(c);
+    const int ns = c->ns, nd = c->nd, npar = 5 * c->m0;
+    // every physical source and detector: W = I, V = I (Sec. 3.2: the full Jacobian once)
+    DevBuf saveW = c->W, saveV = c->V, Wi, Vi;
+    const int save_ls = c->ls, save_ld = c->ld;
+    std::vector<double> eye_s((size_t)ns * ns, 0.0), eye_d((size_t)nd * nd, 0.0);
+    for (int i = 0; i < ns; ++i) eye_s[(size_t)i * ns + i] = 1.0;
+    for (int i = 0; i < nd; ++i) eye_d[(size_t)i * nd + i] = 1.0;
+    int rc = upload(c, Wi, eye_s.data(), eye_s.size() * 8);
+    if (rc == DOT_OK) rc = upload(c, Vi, eye_d.data(), eye_d.size() * 8);
+    if (rc == DOT_OK) {
+        c->W = Wi;
+        c->V = Vi;
+        c->ls = ns;
+        c->ld = nd;
+        invalidate_fields(c);
+        rc = ensure_fields(c);
+    }
+    if (rc == DOT_OK) rc = ensure(c->J, (size_t)nd * ns * npar * esz64(c));
+    if (rc == DOT_OK) {
+        cudaError_t e = pals_chain_jp(cx_, c->p.as<double>(), c->m0, c->gamma, c->nx, c->ny, c->nz, c->h,
+                                      c->wdmu.as<double>(), c->x64.p, c->kp, ns, nd, c->J.as<double>(), c->s);
+        count(c, 1);
+        if (e != cudaSuccess) rc = fail(DOT_ECUDA, std::string("jacobian tensor: ") + cudaGetErrorString(e));
+    }
+    c->W = saveW;
+    c->V = saveV;
+    c->ls = save_ls;
+    c->ld = save_ld;
+    invalidate_fields(c);
+    release(Wi);
+    release(Vi);
+    if (rc != DOT_OK) return rc;
+    DevBuf K, L, G, VW;
+    const int nmax = std::max(nd, ns);
+    rc = ensure(K, (size_t)ns * npar * qd * esz64(c));
+    if (rc == DOT_OK) rc = ensure(L, (size_t)nd * npar * qs * esz64(c));
+    if (rc == DOT_OK) rc = ensure(G, (size_t)nmax * nmax * 8);
+    if (rc == DOT_OK) rc = ensure(VW, (size_t)std::max(nd * qd, ns * qs) * 8);
+    std::vector<double> What, Vhat;
+    int sw = 0;
+    double obj = 0.0;
+    if (rc == DOT_OK)
+        rc = optimize_from_tensor(cx_, c->J.p, nd, ns, npar, qs, qd, maxit, tol, K.p, L.p, G.as<double>(),
+                                  VW.as<double>(), c->s, What, Vhat, &sw, &obj);
+    release(K);
+    release(L);
+    release(G);
+    release(VW);
+    if (rc != DOT_OK) return rc;
+    complement(ns, qs, What, ls - qs, Ytil, W);
+    complement(nd, qd, Vhat, ld - qd, Ztil, V);
+    if (sweeps) *sweeps = sw;
+    if (objective) *objective = obj;
+    return DOT_OK;
+}
+
 int dot_jacobian_mua(dot_ctx* c, double* J) {
     TRY(need_grid(c));
     if (!J) return fail(DOT_EINVAL, "null J");

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 namespace dotk {
 
@@ -129,5 +130,12 @@ cudaError_t pals_chain_gp(const double* p, int m0, double gamma, int nx, int ny,
 cudaError_t pals_chain_jp(bool cplx, const double* p, int m0, double gamma, int nx, int ny, int nz,
                           double h, const double* wdmu, const void* X, int kp, int ls, int ld,
                           double* Jp, cudaStream_t s);
+
+// ---- optimized sources and detectors (optimize.cu)
+int symmetric_eigen(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& Q);
+void complement(int n, int q, const std::vector<double>& What, int m, const double* Ytil, double* out);
+int optimize_from_tensor(bool cplx, const void* Jd, int nd, int ns, int npar, int qs, int qd, int maxit, double tol,
+                         void* scratch_K, void* scratch_L, double* dG, double* dVW, cudaStream_t s,
+                         std::vector<double>& What, std::vector<double>& Vhat, int* sweeps, double* objective);
 
 }  // namespace dotk

@@ -59,6 +59,9 @@ SIGNATURES = {
     "dot_apply": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "dot_set_kernel_timing": [C.c_void_p, C.c_int],
     "dot_set_stencil_path": [C.c_void_p, C.c_int],
+    "dot_optimized_sampling": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_int,
+                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "dot_symeig": [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
     "dot_restrict_misfit_noalloc": [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p],
@@ -271,6 +274,27 @@ def dot_get_stats(ctx) -> dict:
     s = DotStats()
     _check(load().dot_get_stats(ctx, C.byref(s)))
     return s.as_dict()
+
+
+def dot_optimized_sampling(ctx, qs, qd, ns, nd, ls, ld, Ytil=None, Ztil=None, maxit=100, tol=1e-10):
+    W = np.zeros((ns, ls), order="F")
+    V = np.zeros((nd, ld), order="F")
+    Yf = None if Ytil is None else _fortran(Ytil)
+    Zf = None if Ztil is None else _fortran(Ztil)
+    sweeps = C.c_int(0)
+    obj = C.c_double(0.0)
+    _check(load().dot_optimized_sampling(ctx, qs, qd, maxit, tol, ls, _ptr(Yf), ld, _ptr(Zf), _ptr(W), _ptr(V),
+                                         C.byref(sweeps), C.byref(obj)))
+    return W, V, sweeps.value, obj.value
+
+
+def dot_symeig(A):
+    A = _fortran(A)
+    n = A.shape[0]
+    w = np.zeros(n)
+    Q = np.zeros((n, n), order="F")
+    _check(load().dot_symeig(n, _ptr(A), _ptr(w), _ptr(Q)))
+    return w, Q
 
 
 def dot_set_stencil_path(ctx, tma):
