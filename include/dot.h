@@ -79,6 +79,8 @@ typedef struct dot_stats {
     double  ms_solve;        /* last: block Krylov solve                              */
     double  ms_post;         /* last: restriction, misfit, sensitivity, chain rule    */
     int64_t kernel_launches; /* cumulative number of this library's kernel launches   */
+    int32_t tuned_tma;       /* autotuned stencil path (1 TMA, 0 direct, -1 not tuned) */
+    int32_t tuned_blocks_per_sm; /* autotuned blocks per SM of the vector kernels (-1) */
 } dot_stats;
 
 /* Per-kernel device time of the Krylov kernels, accumulated while timing is on.
@@ -206,6 +208,21 @@ int dot_symeig(int n, const double* A, double* evals, double* evecs);
 int dot_get_mua(dot_ctx* ctx, double* mu);
 int dot_get_fields(dot_ctx* ctx, double* U, double* Z);
 int dot_get_stats(dot_ctx* ctx, dot_stats* stats);
+/* Launch options of the block solve.  graphs != 0 (default) replays each steady
+ * batch of Krylov iterations from a CUDA graph captured on the context stream (the
+ * stream must be capturable: not the legacy default stream, no other thread queuing
+ * on it meanwhile).  autotune != 0 (default 0) times the first batches of a solve with
+ * each stencil path and 4, 8 or 16 blocks per SM for the vector kernels, keeps the
+ * fastest for the rest of the solve and for later solves of the same shape; since the
+ * reduction order follows the launch shape, results then agree to rounding (not
+ * bitwise) with an untuned run. */
+int dot_set_launch_options(dot_ctx* ctx, int graphs, int autotune);
+/* Misfit and gradient of several contexts (independent inversions, e.g. uneven grids
+ * and mixed omega) at once: their block solves advance in interleaved batches on
+ * their own streams, so one context's host poll overlaps the others' kernels.  Same
+ * per-context semantics and outputs as dot_gradient (f[i], g[i]); each context must
+ * appear once. */
+int dot_gradient_batch(dot_ctx* const* ctxs, int count, double* f, double* const* g);
 /* Stencil implementation of the block solve: tma != 0 (default) stages p through
  * shared memory with tensor-memory-accelerator copies wherever the block allows it
  * (FP32/complex64 recurrence, nx and ny multiples of 8, padded block width a

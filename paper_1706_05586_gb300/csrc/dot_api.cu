@@ -66,6 +66,57 @@ void release(DevBuf& b) {
     b.bytes = 0;
 }
 
+struct Tuning {
+    bool tma;
+    int blocks_per_sm;
+};
+
+// Host-side state of one block solve in progress.
+struct SolveRun {
+    bool active = false, done = true;
+    int kp = 0, kr = 0;
+    int64_t n = 0;
+    bool mixed = false;
+    ElemKind inner = EK_F64;
+    size_t ei = 8;
+    Launch L{}, Lv{};
+    ColState st{};
+    TmaStencil tma;
+    bool tma_ready = false;
+    OpRaw oi{}, o64{};
+    double delta = 0.0;
+    int maxit = 0;
+    int it = 0, act = 0, upd = 0;
+    bool first = true;
+    Tuning cfg{true, 8};
+    // autotuning: candidates tried one batch each, then the fastest is kept
+    std::vector<Tuning> cands;
+    std::vector<float> cand_ms;
+    int cand_at = -1;
+    bool batch_timed = false;
+    // graph of one steady batch
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_failed = false;
+    float ms_rhs = 0.f;
+};
+
+void run_release_graph(SolveRun& r) {
+    if (r.exec) cudaGraphExecDestroy(r.exec);
+    if (r.graph) cudaGraphDestroy(r.graph);
+    r.exec = nullptr;
+    r.graph = nullptr;
+}
+
+struct TunedChoice {
+    bool valid = false;
+    int64_t n = 0;
+    int kp = 0, inner = 0;
+    bool tma = true;
+    int blocks_per_sm = 8;
+    float ms = 0.f;
+};
+
 }  // namespace
 
 int dotk::record_error(int code, const std::string& msg) { return fail(code, msg); }
@@ -125,6 +176,13 @@ struct dot_ctx {
     DevBuf Tm, S, Rs, f, gmu, gp, J, tmp;
 
     dot_stats stats{};
+
+    // block solve in progress, graph replay and autotuning
+    SolveRun run;
+    bool use_graphs = true;
+    bool autotune = false;
+    TunedChoice tuned;
+    cudaEvent_t bev[2] = {nullptr, nullptr};
 
     // kernel timing (dot_set_kernel_timing)
     bool timing = false;
@@ -284,79 +342,200 @@ int collect_step_timing(dot_ctx* c, int steps, bool first_without_p) {
     return DOT_OK;
 }
 
-// Block solve of [BW | CV] (already in b64) into x64: Jacobi CG/COCG with the
-// recurrence in `inner` precision and reliable updates in FP64.
-// kp is the padded block width (a multiple of 4); padded columns have b = 0 and stay idle.
-int block_solve(dot_ctx* c, int kp, std::vector<int>& iters, std::vector<int>& updates, std::vector<int>& status,
-                std::vector<double>& rr64, std::vector<double>& bb64) {
-    const int64_t n = c->n;
-    const size_t nk = (size_t)n * kp;
-    const bool mixed = c->prec == DOT_PREC_MIXED;
-    const ElemKind inner = cplx(c) ? (mixed ? EK_C64 : EK_C128) : (mixed ? EK_F32 : EK_F64);
-    const size_t ei = mixed ? esz32(c) : esz64(c);
-    const Launch L = krylov_launch(n, kp, c->num_sms);
-    const Launch Lv = vector_launch(n, kp, vector_width(inner), c->num_sms);
-    ColState st;
-    TRY(alloc_colstate(c, kp, std::max(L.grid, Lv.grid), &st));
-    for (DevBuf* b : {&c->xi, &c->ri, &c->pi, &c->qi}) TRY(ensure(*b, nk * ei));
-    const OpRaw oi = mixed ? op32(c) : op64(c), o64 = op64(c);
-    const double delta = mixed ? c->delta : 0.0;
-    TmaStencil tma;
-    const bool use_tma = c->use_tma && tma_stencil_eligible(inner, c->nx, c->ny, kp);
-    if (use_tma) CK(tma_stencil_prepare(inner, c->pi.p, c->nx, c->ny, c->nz, kp, c->num_sms, &tma));
-    const int maxit = c->maxit > 0 ? c->maxit : 10 * (c->nx + c->ny + c->nz);
-    CK(solve_start(inner, oi, c->b64.p, c->x64.p, c->xi.p, c->ri.p, c->pi.p, n, kp, st, c->rtol, L, c->s));
-    count(c, 2);
-    int act = 0, upd = 0, it = 0;
-    TRY(read_counts(c, st, &act, &upd));
-    bool first = true;
-    while (act > 0 && it < maxit + 2 * kPoll) {
-        const bool first_batch = first;
-        for (int m = 0; m < kPoll; ++m) {
-            CK(kry_step(inner, oi, c->xi.p, c->ri.p, c->pi.p, c->qi.p, n, kp, st, delta, maxit, !first, Lv,
-                        use_tma ? &tma : nullptr, c->s, c->timing ? &c->tev[4 * m] : nullptr));
-            count(c, first ? 2 : 3);
-            first = false;
-        }
-        it += kPoll;
-        TRY(read_counts(c, st, &act, &upd));
-        if (c->timing) TRY(collect_step_timing(c, kPoll, first_batch));
-        if (upd > 0) {
-            if (c->timing) CK(cudaEventRecord(c->tev[32], c->s));
-            CK(solve_refresh(inner, oi, o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, c->ri.p, n, kp, st, c->rtol,
-                             maxit, L, c->num_sms, c->s));
-            count(c, 3);
-            if (c->timing) {
-                CK(cudaEventRecord(c->tev[33], c->s));
-                CK(cudaEventSynchronize(c->tev[33]));
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, c->tev[32], c->tev[33]));
-                c->kt.ms[3] += ms;
-                c->kt.launches[3] += 3;
-                c->kt.bytes[3] += (double)upd * n * (6.0 * esz64(c) + 3.0 * ei) + (double)n * 4.0 * 8.0;
+// ------------------------------------------------------------ resumable solve
+// A block solve of [BW | CV] (already in b64) into x64 runs as begin / (advance, poll)*
+// / end, so that several contexts can interleave their solves on their own streams
+// (dot_gradient_batch) while one context simply loops.  advance() queues one batch of
+// kPoll iterations (replayed from a CUDA graph once the launch configuration is
+// settled); poll() waits for the context's stream, reads the column counters and runs a
+// reliable-update round if a column asked for one.
+
+int apply_tuning(dot_ctx* c, SolveRun& r, const Tuning& t) {
+    r.cfg = t;
+    r.Lv = vector_launch(r.n, r.kp, vector_width(r.inner), c->num_sms);
+    const int64_t need = (r.n + r.Lv.slots - 1) / r.Lv.slots;
+    const int64_t g = (int64_t)c->num_sms * t.blocks_per_sm;
+    r.Lv.grid = (int)std::max<int64_t>(1, std::min(need, g));
+    if (t.tma && !r.tma_ready) {
+        CK(tma_stencil_prepare(r.inner, c->pi.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma));
+        r.tma_ready = true;
+    }
+    run_release_graph(r);
+    r.graph_failed = false;
+    return DOT_OK;
+}
+
+int solve_begin(dot_ctx* c, int kp, int kr) {
+    SolveRun& r = c->run;
+    run_release_graph(r);
+    r = SolveRun();
+    r.active = true;
+    r.done = false;
+    r.kp = kp;
+    r.kr = kr;
+    r.n = c->n;
+    r.mixed = c->prec == DOT_PREC_MIXED;
+    r.inner = cplx(c) ? (r.mixed ? EK_C64 : EK_C128) : (r.mixed ? EK_F32 : EK_F64);
+    r.ei = r.mixed ? esz32(c) : esz64(c);
+    r.L = krylov_launch(r.n, kp, c->num_sms);
+    const Launch Lmax = vector_launch(r.n, kp, vector_width(r.inner), c->num_sms);
+    const int gmax = (int)std::min<int64_t>((r.n + Lmax.slots - 1) / Lmax.slots, (int64_t)c->num_sms * 16);
+    TRY(alloc_colstate(c, kp, std::max(r.L.grid, std::max(gmax, 1)), &r.st));
+    for (DevBuf* b : {&c->xi, &c->ri, &c->pi, &c->qi}) TRY(ensure(*b, (size_t)r.n * kp * r.ei));
+    r.oi = r.mixed ? op32(c) : op64(c);
+    r.o64 = op64(c);
+    r.delta = r.mixed ? c->delta : 0.0;
+    r.maxit = c->maxit > 0 ? c->maxit : 10 * (c->nx + c->ny + c->nz);
+    const bool tma_ok = tma_stencil_eligible(r.inner, c->nx, c->ny, kp);
+    Tuning base{c->use_tma && tma_ok, 8};
+    if (c->autotune) {
+        const bool have = c->tuned.valid && c->tuned.n == r.n && c->tuned.kp == kp && c->tuned.inner == (int)r.inner;
+        if (have) {
+            base = Tuning{c->tuned.tma && tma_ok, c->tuned.blocks_per_sm};
+        } else {
+            for (int bps : {4, 8, 16}) {
+                r.cands.push_back(Tuning{false, bps});
+                if (tma_ok) r.cands.push_back(Tuning{true, bps});
             }
-            TRY(read_counts(c, st, &act, &upd));
+            r.cand_ms.assign(r.cands.size(), 0.f);
+            r.cand_at = 0;
+            base = r.cands[0];
         }
     }
-    iters.resize(kp);
-    updates.resize(kp);
-    status.resize(kp);
-    rr64.resize(kp);
-    bb64.resize(kp);
-    CK(cudaMemcpyAsync(status.data(), st.status, kp * 4, cudaMemcpyDeviceToHost, c->s));
+    TRY(apply_tuning(c, r, base));
+    CK(solve_start(r.inner, r.oi, c->b64.p, c->x64.p, c->xi.p, c->ri.p, c->pi.p, r.n, kp, r.st, c->rtol, r.L, c->s));
+    count(c, 2);
+    TRY(read_counts(c, r.st, &r.act, &r.upd));
+    r.done = r.act == 0;
+    return DOT_OK;
+}
+
+int launch_batch(dot_ctx* c, SolveRun& r, bool first_batch) {
+    for (int m = 0; m < kPoll; ++m) {
+        const bool with_p = !(first_batch && m == 0);
+        CK(kry_step(r.inner, r.oi, c->xi.p, c->ri.p, c->pi.p, c->qi.p, r.n, r.kp, r.st, r.delta, r.maxit, with_p, r.Lv,
+                    r.cfg.tma ? &r.tma : nullptr, c->s, c->timing ? &c->tev[4 * m] : nullptr));
+    }
+    return DOT_OK;
+}
+
+// Queue one batch of kPoll iterations.
+int solve_advance(dot_ctx* c) {
+    SolveRun& r = c->run;
+    if (r.done) return DOT_OK;
+    const bool first_batch = r.first;
+    const bool tuning = r.cand_at >= 0;
+    r.batch_timed = tuning;
+    if (tuning) CK(cudaEventRecord(c->bev[0], c->s));
+    const bool use_graph = c->use_graphs && !first_batch && !tuning && !r.graph_failed;
+    if (use_graph && !r.exec) {
+        // capture one steady batch of the settled configuration; fall back to direct
+        // launches if the stream cannot be captured
+        cudaError_t e = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const int rc = launch_batch(c, r, false);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(c->s, &g);
+            if (rc == DOT_OK && e == cudaSuccess && g) {
+                r.graph = g;
+                e = cudaGraphInstantiate(&r.exec, g, 0);
+            }
+            if (rc != DOT_OK || e != cudaSuccess || !r.exec) {
+                cudaGetLastError();
+                run_release_graph(r);
+                r.graph_failed = true;
+            }
+        } else {
+            cudaGetLastError();
+            r.graph_failed = true;
+        }
+    }
+    if (use_graph && r.exec) {
+        CK(cudaGraphLaunch(r.exec, c->s));
+    } else {
+        TRY(launch_batch(c, r, first_batch));
+    }
+    count(c, kPoll * 3 - (first_batch ? 1 : 0));
+    if (tuning) CK(cudaEventRecord(c->bev[1], c->s));
+    r.first = false;
+    r.it += kPoll;
+    return DOT_OK;
+}
+
+// Wait for the queued batch, read the counters, refresh if asked, and decide completion.
+int solve_poll(dot_ctx* c) {
+    SolveRun& r = c->run;
+    if (r.done) return DOT_OK;
+    const bool first_batch = r.it == kPoll;
+    TRY(read_counts(c, r.st, &r.act, &r.upd));
+    if (c->timing) TRY(collect_step_timing(c, kPoll, first_batch));
+    if (r.batch_timed) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->bev[0], c->bev[1]));
+        if (!first_batch) {  // the first batch is one launch short: time the candidate again
+            r.cand_ms[r.cand_at] = ms;
+            ++r.cand_at;
+        }
+        if (r.cand_at >= (int)r.cands.size()) {
+            int best = 0;
+            for (int i = 1; i < (int)r.cands.size(); ++i)
+                if (r.cand_ms[i] < r.cand_ms[best]) best = i;
+            c->tuned.valid = true;
+            c->tuned.n = r.n;
+            c->tuned.kp = r.kp;
+            c->tuned.inner = (int)r.inner;
+            c->tuned.tma = r.cands[best].tma;
+            c->tuned.blocks_per_sm = r.cands[best].blocks_per_sm;
+            c->tuned.ms = r.cand_ms[best];
+            r.cand_at = -1;
+            TRY(apply_tuning(c, r, r.cands[best]));
+        } else {
+            TRY(apply_tuning(c, r, r.cands[r.cand_at]));
+        }
+        r.batch_timed = false;
+    }
+    if (r.upd > 0) {
+        if (c->timing) CK(cudaEventRecord(c->tev[32], c->s));
+        CK(solve_refresh(r.inner, r.oi, r.o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, c->ri.p, r.n, r.kp, r.st,
+                         c->rtol, r.maxit, r.L, c->num_sms, c->s));
+        count(c, 3);
+        if (c->timing) {
+            CK(cudaEventRecord(c->tev[33], c->s));
+            CK(cudaEventSynchronize(c->tev[33]));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->tev[32], c->tev[33]));
+            c->kt.ms[3] += ms;
+            c->kt.launches[3] += 3;
+            c->kt.bytes[3] += (double)r.upd * r.n * (6.0 * esz64(c) + 3.0 * r.ei) + (double)r.n * 4.0 * 8.0;
+        }
+        TRY(read_counts(c, r.st, &r.act, &r.upd));
+    }
+    r.done = r.act == 0 || r.it >= r.maxit + 2 * kPoll;
+    return DOT_OK;
+}
+
+// Promote the last corrections, read the per-column results and fill the statistics.
+int solve_end(dot_ctx* c) {
+    SolveRun& r = c->run;
+    const int kp = r.kp;
+    std::vector<int> iters(kp), updates(kp), status(kp), active(kp);
+    std::vector<double> rr(kp), bb(kp);
+    CK(cudaMemcpyAsync(status.data(), r.st.status, kp * 4, cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
-    bool any_bad = act > 0;
+    bool any_bad = r.act > 0;
     for (int j = 0; j < kp; ++j) any_bad = any_bad || status[j] != DOT_OK;
-    CK(solve_finish(inner, o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, n, kp, st, any_bad, L, c->num_sms, c->s));
+    CK(solve_finish(r.inner, r.o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, r.n, kp, r.st, any_bad, r.L, c->num_sms,
+                    c->s));
     count(c, any_bad ? 2 : 1);
-    CK(cudaMemcpyAsync(iters.data(), st.iters, kp * 4, cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(updates.data(), st.updates, kp * 4, cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(status.data(), st.status, kp * 4, cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(rr64.data(), st.rr64, kp * 8, cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(bb64.data(), st.bb64, kp * 8, cudaMemcpyDeviceToHost, c->s));
-    std::vector<int> active(kp);
-    CK(cudaMemcpyAsync(active.data(), st.active, kp * 4, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(iters.data(), r.st.iters, kp * 4, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(updates.data(), r.st.updates, kp * 4, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(status.data(), r.st.status, kp * 4, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(rr.data(), r.st.rr64, kp * 8, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(bb.data(), r.st.bb64, kp * 8, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(active.data(), r.st.active, kp * 4, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaEventRecord(c->ev[2], c->s));
     CK(cudaStreamSynchronize(c->s));
+    run_release_graph(r);
     for (int j = 0; j < kp; ++j)
         if (active[j] && status[j] == DOT_OK) status[j] = DOT_ENOTCONV;
     if (c->timing) {
@@ -369,15 +548,47 @@ int block_solve(dot_ctx* c, int kp, std::vector<int>& iters, std::vector<int>& u
             ci += iters[j];
             itmax = std::max(itmax, iters[j]);
         }
-        const double nn = (double)n, rs = mixed ? 4.0 : 8.0;
-        c->kt.bytes[0] += ci * nn * 2.0 * ei + itmax * nn * 4.0 * rs;
-        c->kt.bytes[1] += ci * nn * 6.0 * ei + itmax * nn * ei;
-        c->kt.bytes[2] += ci * nn * 3.0 * ei + itmax * nn * ei;
+        const double nn = (double)r.n, rs = r.mixed ? 4.0 : 8.0;
+        c->kt.bytes[0] += ci * nn * 2.0 * r.ei + itmax * nn * 4.0 * rs;
+        c->kt.bytes[1] += ci * nn * 6.0 * r.ei + itmax * nn * r.ei;
+        c->kt.bytes[2] += ci * nn * 3.0 * r.ei + itmax * nn * r.ei;
     }
+    float ms_solve = 0;
+    cudaEventElapsedTime(&ms_solve, c->ev[1], c->ev[2]);
+    int st_all = DOT_OK;
+    double relmax = 0.0;
+    int itmax = 0, updmax = 0;
+    int64_t itsum = 0;
+    for (int j = 0; j < r.kr; ++j) {
+        if (status[j] == DOT_EBREAKDOWN) st_all = DOT_EBREAKDOWN;
+        else if (status[j] == DOT_ENOTCONV && st_all == DOT_OK) st_all = DOT_ENOTCONV;
+        if (bb[j] > 0) relmax = std::max(relmax, std::sqrt(rr[j] / bb[j]));
+        itmax = std::max(itmax, iters[j]);
+        updmax = std::max(updmax, updates[j]);
+        itsum += iters[j];
+    }
+    c->stats.k = r.kr;
+    c->stats.iters_max = itmax;
+    c->stats.iters_sum = itsum;
+    c->stats.outer_steps = updmax;
+    c->stats.status = st_all;
+    c->stats.relres_max = relmax;
+    c->stats.columns_solved += r.kr;
+    c->stats.block_solves += 1;
+    c->stats.ms_setup = r.ms_rhs;
+    c->stats.ms_solve = ms_solve;
+    c->kp = kp;
+    c->fields_status = st_all;
+    c->fields_valid = true;
+    c->post_valid = false;
+    r.active = false;
     return DOT_OK;
 }
 
-int ensure_fields(dot_ctx* c) {
+// Checks, right-hand sides and the start of the block solve; nothing to do when the
+// fields are already valid.
+int fields_begin(dot_ctx* c) {
+    c->run.active = false;
     if (c->fields_valid) return DOT_OK;
     TRY(ensure_coefficients(c));
     if (c->ns == 0) return fail(DOT_ESTATE, "dot_set_sources has not been called");
@@ -397,41 +608,28 @@ int ensure_fields(dot_ctx* c) {
                  c->ld, n, kp, c->b64.p, c->s));
     count(c, 1);
     CK(cudaEventRecord(c->ev[1], c->s));
-    std::vector<int> iters, updates, status;
-    std::vector<double> rr, bb;
-    TRY(block_solve(c, kp, iters, updates, status, rr, bb));
-    CK(cudaEventRecord(c->ev[2], c->s));
-    CK(cudaEventSynchronize(c->ev[2]));
-    float ms_rhs = 0, ms_solve = 0;
+    TRY(solve_begin(c, kp, kr));
+    float ms_rhs = 0.f;
     cudaEventElapsedTime(&ms_rhs, c->ev[0], c->ev[1]);
-    cudaEventElapsedTime(&ms_solve, c->ev[1], c->ev[2]);
-    int st_all = DOT_OK;
-    double relmax = 0.0;
-    int itmax = 0, updmax = 0;
-    int64_t itsum = 0;
-    for (int j = 0; j < kr; ++j) {
-        if (status[j] == DOT_EBREAKDOWN) st_all = DOT_EBREAKDOWN;
-        else if (status[j] == DOT_ENOTCONV && st_all == DOT_OK) st_all = DOT_ENOTCONV;
-        if (bb[j] > 0) relmax = std::max(relmax, std::sqrt(rr[j] / bb[j]));
-        itmax = std::max(itmax, iters[j]);
-        updmax = std::max(updmax, updates[j]);
-        itsum += iters[j];
-    }
-    c->stats.k = kr;
-    c->stats.iters_max = itmax;
-    c->stats.iters_sum = itsum;
-    c->stats.outer_steps = updmax;
-    c->stats.status = st_all;
-    c->stats.relres_max = relmax;
-    c->stats.columns_solved += kr;
-    c->stats.block_solves += 1;
-    c->stats.ms_setup = ms_rhs;
-    c->stats.ms_solve = ms_solve;
-    c->kp = kp;
-    c->fields_status = st_all;
-    c->fields_valid = true;
-    c->post_valid = false;
+    c->run.ms_rhs = ms_rhs;
     return DOT_OK;
+}
+
+bool fields_pending(dot_ctx* c) { return c->run.active && !c->run.done; }
+
+int fields_finish(dot_ctx* c) {
+    if (!c->run.active) return DOT_OK;
+    return solve_end(c);
+}
+
+int ensure_fields(dot_ctx* c) {
+    if (c->fields_valid) return DOT_OK;
+    TRY(fields_begin(c));
+    while (fields_pending(c)) {
+        TRY(solve_advance(c));
+        TRY(solve_poll(c));
+    }
+    return fields_finish(c);
 }
 
 int ensure_projection(dot_ctx* c) {
@@ -540,6 +738,7 @@ int dot_create(dot_ctx** out, int device) {
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_flag, 8 * sizeof(int));
     for (int t = 0; t < 4 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->ev[t]);
     for (int t = 0; t < 34 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->tev[t]);
+    for (int t = 0; t < 2 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->bev[t]);
     if (e != cudaSuccess) {
         dot_destroy(c);
         return fail(DOT_ECUDA, std::string("context creation: ") + cudaGetErrorString(e));
@@ -562,6 +761,9 @@ int dot_destroy(dot_ctx* c) {
         if (c->ev[t]) cudaEventDestroy(c->ev[t]);
     for (int t = 0; t < 34; ++t)
         if (c->tev[t]) cudaEventDestroy(c->tev[t]);
+    for (int t = 0; t < 2; ++t)
+        if (c->bev[t]) cudaEventDestroy(c->bev[t]);
+    run_release_graph(c->run);
     if (c->h_flag) cudaFreeHost(c->h_flag);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
@@ -984,6 +1186,59 @@ int dot_get_fields(dot_ctx* c, double* U, double* Z) {
 int dot_get_stats(dot_ctx* c, dot_stats* out) {
     if (!c || !out) return fail(DOT_EINVAL, "null argument");
     *out = c->stats;
+    out->tuned_tma = c->tuned.valid ? (c->tuned.tma ? 1 : 0) : -1;
+    out->tuned_blocks_per_sm = c->tuned.valid ? c->tuned.blocks_per_sm : -1;
+    return DOT_OK;
+}
+
+int dot_set_launch_options(dot_ctx* c, int graphs, int autotune) {
+    TRY(need_ctx(c));
+    c->use_graphs = graphs != 0;
+    c->autotune = autotune != 0;
+    invalidate_fields(c);
+    return DOT_OK;
+}
+
+int dot_gradient_batch(dot_ctx* const* ctxs, int count, double* f, double* const* g) {
+    if (count < 1 || !ctxs || !f || !g) return fail(DOT_EINVAL, "bad batch arguments");
+    for (int i = 0; i < count; ++i) {
+        dot_ctx* c = ctxs[i];
+        TRY(need_grid(c));
+        if (!c->M_set) return fail(DOT_ESTATE, "dot_set_data has not been called on a batch member");
+        if (!g[i]) return fail(DOT_EINVAL, "null gradient output");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return fail(DOT_EINVAL, "a context appears twice in the batch");
+    }
+    // start every member's solve, then interleave their batches: while one stream is
+    // polled the others keep the GPU busy
+    for (int i = 0; i < count; ++i) {
+        TRY(need_ctx(ctxs[i]));
+        TRY(fields_begin(ctxs[i]));
+    }
+    bool pending = true;
+    while (pending) {
+        pending = false;
+        for (int i = 0; i < count; ++i)
+            if (fields_pending(ctxs[i])) {
+                TRY(need_ctx(ctxs[i]));
+                TRY(solve_advance(ctxs[i]));
+                pending = true;
+            }
+        for (int i = 0; i < count; ++i)
+            if (fields_pending(ctxs[i])) {
+                TRY(need_ctx(ctxs[i]));
+                TRY(solve_poll(ctxs[i]));
+            }
+    }
+    int worst = DOT_OK;
+    for (int i = 0; i < count; ++i) {
+        TRY(need_ctx(ctxs[i]));
+        TRY(fields_finish(ctxs[i]));
+        const int rc = dot_gradient(ctxs[i], f + i, g[i]);
+        if (rc != DOT_OK && rc != DOT_ENOTCONV && rc != DOT_EBREAKDOWN) return rc;
+        if (rc != DOT_OK && worst == DOT_OK) worst = rc;
+    }
+    if (worst != DOT_OK) return fail(worst, "a batch member's block solve did not converge in every column");
     return DOT_OK;
 }
 

@@ -59,6 +59,8 @@ SIGNATURES = {
     "dot_apply": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "dot_set_kernel_timing": [C.c_void_p, C.c_int],
     "dot_set_stencil_path": [C.c_void_p, C.c_int],
+    "dot_set_launch_options": [C.c_void_p, C.c_int, C.c_int],
+    "dot_gradient_batch": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "dot_optimized_sampling": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_int,
                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "dot_symeig": [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -74,7 +76,8 @@ class DotStats(C.Structure):
     _fields_ = [("k", C.c_int32), ("iters_max", C.c_int32), ("iters_sum", C.c_int64),
                 ("outer_steps", C.c_int32), ("status", C.c_int32), ("relres_max", C.c_double),
                 ("columns_solved", C.c_int64), ("block_solves", C.c_int64), ("ms_setup", C.c_double),
-                ("ms_solve", C.c_double), ("ms_post", C.c_double), ("kernel_launches", C.c_int64)]
+                ("ms_solve", C.c_double), ("ms_post", C.c_double), ("kernel_launches", C.c_int64),
+                ("tuned_tma", C.c_int32), ("tuned_blocks_per_sm", C.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -295,6 +298,21 @@ def dot_symeig(A):
     Q = np.zeros((n, n), order="F")
     _check(load().dot_symeig(n, _ptr(A), _ptr(w), _ptr(Q)))
     return w, Q
+
+
+def dot_set_launch_options(ctx, graphs=True, autotune=False):
+    return _check(load().dot_set_launch_options(ctx, int(bool(graphs)), int(bool(autotune))))
+
+
+def dot_gradient_batch(ctxs, ngs, allow=()):
+    """Misfit and gradient of several contexts; ngs[i] is the gradient length of ctxs[i]."""
+    n = len(ctxs)
+    handles = (C.c_void_p * n)(*[c.value if hasattr(c, "value") else c for c in ctxs])
+    f = np.zeros(n)
+    gs = [np.zeros(m) for m in ngs]
+    gp = (C.c_void_p * n)(*[g.ctypes.data for g in gs])
+    rc = _check(load().dot_gradient_batch(C.cast(handles, C.c_void_p), n, _ptr(f), C.cast(gp, C.c_void_p)), allow)
+    return f, gs, rc
 
 
 def dot_set_stencil_path(ctx, tma):

@@ -103,6 +103,15 @@ WORKLOADS = {
 }
 
 
+# Eight independent inversions with uneven grids n x n x n/2 (h = 8/n cm, 8 x 8 x 4 cm
+# box, 96 <= n <= 256, 23,281,664 cells in all) and alternating omega = 0 / 100 MHz,
+# each with 1,024 sources and 1,024 detectors sampled by 40 + 40 columns.
+BATCH8 = tuple(
+    Workload(f"batch8_{n}", n, n, n // 2, 8.0 / n, (0.0 if i % 2 == 0 else OMEGA_NU_100MHZ), (32, 32), (32, 32),
+             40, 40, 125, sampling="gaussian", rtol=1e-10, seed_index=20 + i)
+    for i, n in enumerate((96, 112, 128, 144, 160, 192, 224, 256)))
+
+
 def small_workload(nx, ny, nz, h, *, omega_nu=0.0, src_grid=(2, 2), det_grid=(2, 2), ls=1, ld=1,
                    m0=4, sampling="rademacher", bc=(ROBIN,) * 6, seed_index=11, rbf_radius=None,
                    gamma=1e-2, cutoff=0.0, noise=0.01, name=None) -> Workload:

@@ -1,0 +1,83 @@
+"""Several independent inversions in one call (dot_gradient_batch), CUDA-graph replay
+of the iteration batches, and the launch autotuner: the batch reproduces each
+context's own evaluation bitwise (same kernels, same launch shapes), graph replay is
+bitwise identical to direct launches, and autotuned launches agree to rounding."""
+import numpy as np
+import pytest
+
+from paper_1706_05586_gb300 import dot as D
+from paper_1706_05586_gb300 import synth
+from tests import problem
+from tests.gpu_setup import configure, rel
+
+pytestmark = pytest.mark.gpu
+
+MEMBERS = [
+    synth.small_workload(16, 16, 9, 0.3, src_grid=(4, 4), det_grid=(4, 4), ls=16, ld=16, m0=4, sampling="gaussian",
+                         seed_index=66),                                   # TMA-eligible, real
+    synth.small_workload(11, 6, 7, 0.35, omega_nu=0.3, src_grid=(3, 1), det_grid=(2, 2), ls=3, ld=2, m0=5,
+                         sampling="gaussian", seed_index=62),              # ragged, complex
+    synth.small_workload(24, 16, 10, 0.3, omega_nu=0.4, src_grid=(4, 4), det_grid=(4, 4), ls=16, ld=16, m0=5,
+                         sampling="gaussian", seed_index=65),              # TMA-eligible, complex
+]
+
+
+@pytest.fixture(scope="module")
+def problems():
+    return [problem.build(w) for w in MEMBERS]
+
+
+def _single(pb, prec, rtol, graphs=True, autotune=False):
+    h = D.dot_create(0)
+    try:
+        configure(h, pb, p=pb.inp.p0, prec=prec, rtol=rtol)
+        D.dot_set_launch_options(h, graphs, autotune)
+        f, g, _ = D.dot_gradient(h, pb.wl.np_)
+        return f, g, D.dot_get_stats(h)
+    finally:
+        D.dot_destroy(h)
+
+
+@pytest.mark.parametrize("prec,rtol", [(D.PREC_MIXED, 1e-12), (D.PREC_FP64, 1e-13)])
+def test_batch_matches_members_bitwise(problems, prec, rtol):
+    hs = [D.dot_create(0) for _ in problems]
+    try:
+        for h, pb in zip(hs, problems):
+            configure(h, pb, p=pb.inp.p0, prec=prec, rtol=rtol)
+        f, gs, rc = D.dot_gradient_batch(hs, [pb.wl.np_ for pb in problems])
+        assert rc == D.DOT_OK
+    finally:
+        for h in hs:
+            D.dot_destroy(h)
+    for i, pb in enumerate(problems):
+        f1, g1, _ = _single(pb, prec, rtol)
+        assert f[i] == f1 and np.array_equal(gs[i], g1)
+
+
+def test_graph_replay_is_bitwise_identical(problems):
+    for pb in problems:
+        a = _single(pb, D.PREC_MIXED, 1e-12, graphs=True)
+        b = _single(pb, D.PREC_MIXED, 1e-12, graphs=False)
+        assert a[0] == b[0] and np.array_equal(a[1], b[1])
+        assert a[2]["iters_max"] == b[2]["iters_max"]
+
+
+def test_autotuned_launches_agree(problems):
+    for pb in problems:
+        ref = _single(pb, D.PREC_MIXED, 1e-12)
+        tuned = _single(pb, D.PREC_MIXED, 1e-12, autotune=True)
+        assert abs(tuned[0] - ref[0]) <= 1e-9 * abs(ref[0])
+        assert rel(tuned[1], ref[1]) <= 1e-7
+        st = tuned[2]
+        assert st["tuned_blocks_per_sm"] in (4, 8, 16) and st["tuned_tma"] in (0, 1)
+
+
+def test_batch_rejects_duplicates(problems):
+    h = D.dot_create(0)
+    try:
+        configure(h, problems[1], p=problems[1].inp.p0)
+        with pytest.raises(D.DotError) as e:
+            D.dot_gradient_batch([h, h], [problems[1].wl.np_] * 2)
+        assert e.value.code == D.DOT_EINVAL
+    finally:
+        D.dot_destroy(h)
