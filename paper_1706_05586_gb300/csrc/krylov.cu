@@ -548,25 +548,37 @@ cudaError_t solve_start(ElemKind inner, const OpRaw& o, const void* b64, void* x
     return cudaGetLastError();
 }
 
+// Timing events around the launches of one iteration.  Inside a stream capture a plain
+// record only orders work, so the capture records them as event nodes of the graph
+// instead; every replay then records them like a direct launch would.
+static void record_timing(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, s);
+}
+
 cudaError_t kry_step(ElemKind inner, const OpRaw& o, void* x, void* r, void* p, void* q, int64_t n, int kp,
                      const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv,
                      const TmaStencil* tma, cudaStream_t s, cudaEvent_t* ev) {
     DOT_DISPATCH2(inner, {
         Op<T> op = make_op<T>(o);
         const size_t sm = red_smem(Lv, kp);
-        if (ev) cudaEventRecord(ev[0], s);
+        if (ev) record_timing(ev[0], s);
         if (with_p) k_p<T><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, (T*)p, n, kp, Lv.slots, st);
-        if (ev) cudaEventRecord(ev[1], s);
+        if (ev) record_timing(ev[1], s);
         if (tma) {
             const cudaError_t e = tma_stencil_launch(inner, o, *tma, q, kp, st, s);
             if (e != cudaSuccess) return e;
         } else {
             k_pq<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)p, (T*)q, kp, Lv.slots, st);
         }
-        if (ev) cudaEventRecord(ev[2], s);
+        if (ev) record_timing(ev[2], s);
         k_xr<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)p, (const T*)q, (T*)x, (T*)r, n, kp, Lv.slots, st,
                                                  delta, maxit);
-        if (ev) cudaEventRecord(ev[3], s);
+        if (ev) record_timing(ev[3], s);
         (void)sizeof(T64);
     });
     return cudaGetLastError();

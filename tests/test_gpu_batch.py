@@ -81,3 +81,48 @@ def test_batch_rejects_duplicates(problems):
         assert e.value.code == D.DOT_EINVAL
     finally:
         D.dot_destroy(h)
+
+
+def _timed(pb, graphs):
+    h = D.dot_create(0)
+    try:
+        configure(h, pb, p=pb.inp.p0, prec=D.PREC_MIXED, rtol=1e-12)
+        D.dot_set_launch_options(h, graphs, False)
+        D.dot_set_kernel_timing(h, 1)
+        f, g, _ = D.dot_gradient(h, pb.wl.np_)
+        return f, g, D.dot_get_kernel_timing(h)
+    finally:
+        D.dot_destroy(h)
+
+
+def test_kernel_timing_under_graph_replay(problems):
+    # per-launch timing events are part of the captured graph: the same launches are
+    # counted with and without replay, every timed kernel has a positive duration,
+    # and timing changes no result
+    for pb in problems:
+        fa, ga, ka = _timed(pb, True)
+        fb, gb, kb = _timed(pb, False)
+        assert fa == fb and np.array_equal(ga, gb)
+        for nm in ka:
+            assert ka[nm]["launches"] == kb[nm]["launches"]
+            if ka[nm]["launches"]:
+                assert ka[nm]["ms"] > 0.0
+
+
+def test_batch_with_kernel_timing(problems):
+    hs = [D.dot_create(0) for _ in problems]
+    try:
+        for h, pb in zip(hs, problems):
+            configure(h, pb, p=pb.inp.p0, prec=D.PREC_MIXED, rtol=1e-12)
+            D.dot_set_kernel_timing(h, 1)
+        f, gs, rc = D.dot_gradient_batch(hs, [pb.wl.np_ for pb in problems])
+        assert rc == D.DOT_OK
+        for h in hs:
+            kt = D.dot_get_kernel_timing(h)
+            assert sum(kt[nm]["launches"] for nm in kt) > 0
+    finally:
+        for h in hs:
+            D.dot_destroy(h)
+    for i, pb in enumerate(problems):
+        f1, g1, _ = _single(pb, D.PREC_MIXED, 1e-12)
+        assert f[i] == f1 and np.array_equal(gs[i], g1)
