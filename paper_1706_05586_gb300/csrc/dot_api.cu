@@ -167,7 +167,7 @@ struct dot_ctx {
     // vectors x~, r~, p, q in the inner precision
     DevBuf b64, x64, r64, xi, ri, pi, qi;
     // per-column state (one allocation) and per-block partial sums
-    DevBuf colbuf, partA, partB;
+    DevBuf colbuf, partA, partB, gcount;
     bool fields_valid = false;
     int fields_status = DOT_OK;
     int kp = 0;
@@ -276,9 +276,12 @@ int alloc_colstate(dot_ctx* c, int kp, int max_grid, ColState* st) {
     const size_t n16 = (size_t)kp * 16, n8 = (size_t)kp * 8, n4 = (size_t)kp * 4;
     const size_t bytes = 4 * n16 + 7 * n8 + 6 * n4 + 64;
     TRY(ensure(c->colbuf, bytes));
-    TRY(ensure(c->partA, (size_t)max_grid * kp * 16));
-    TRY(ensure(c->partB, (size_t)max_grid * kp * 8));
+    const size_t groups = ((size_t)max_grid + kReduceGroup - 1) / kReduceGroup;
+    TRY(ensure(c->partA, ((size_t)max_grid + groups) * kp * 16));
+    TRY(ensure(c->partB, ((size_t)max_grid + groups) * kp * 8));
+    TRY(ensure(c->gcount, groups * 4));
     CK(cudaMemsetAsync(c->colbuf.p, 0, bytes, c->s));
+    CK(cudaMemsetAsync(c->gcount.p, 0, groups * 4, c->s));
     char* q = c->colbuf.as<char>();
     auto take = [&](size_t b) {
         char* r = q;
@@ -309,6 +312,9 @@ int alloc_colstate(dot_ctx* c, int kp, int max_grid, ColState* st) {
     st->error = misc + 6;
     st->partA = c->partA.as<double2>();
     st->partB = c->partB.as<double>();
+    st->groupA = st->partA + (size_t)max_grid * kp;
+    st->groupB = st->partB + (size_t)max_grid * kp;
+    st->gcount = c->gcount.as<unsigned>();
     return DOT_OK;
 }
 
@@ -357,7 +363,7 @@ int apply_tuning(dot_ctx* c, SolveRun& r, const Tuning& t) {
     const int64_t g = (int64_t)c->num_sms * t.blocks_per_sm;
     r.Lv.grid = (int)std::max<int64_t>(1, std::min(need, g));
     if (t.tma && !r.tma_ready) {
-        CK(tma_stencil_prepare(r.inner, c->pi.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma));
+        CK(tma_stencil_prepare(r.inner, c->pi.p, c->cf32.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma));
         r.tma_ready = true;
     }
     run_release_graph(r);
@@ -496,8 +502,8 @@ int solve_poll(dot_ctx* c) {
     }
     if (r.upd > 0) {
         if (c->timing) CK(cudaEventRecord(c->tev[32], c->s));
-        CK(solve_refresh(r.inner, r.oi, r.o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, c->ri.p, r.n, r.kp, r.st,
-                         c->rtol, r.maxit, r.L, c->num_sms, c->s));
+        CK(solve_refresh(r.inner, r.oi, r.o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, c->ri.p, c->pi.p, r.n, r.kp,
+                         r.st, c->rtol, r.maxit, r.L, c->num_sms, c->s));
         count(c, 3);
         if (c->timing) {
             CK(cudaEventRecord(c->tev[33], c->s));
@@ -506,7 +512,7 @@ int solve_poll(dot_ctx* c) {
             CK(cudaEventElapsedTime(&ms, c->tev[32], c->tev[33]));
             c->kt.ms[3] += ms;
             c->kt.launches[3] += 3;
-            c->kt.bytes[3] += (double)r.upd * r.n * (6.0 * esz64(c) + 3.0 * r.ei) + (double)r.n * 4.0 * 8.0;
+            c->kt.bytes[3] += (double)r.act * r.n * (6.0 * esz64(c) + 4.0 * r.ei) + (double)r.n * 4.0 * 8.0;
         }
         TRY(read_counts(c, r.st, &r.act, &r.upd));
     }
@@ -524,7 +530,7 @@ int solve_end(dot_ctx* c) {
     CK(cudaStreamSynchronize(c->s));
     bool any_bad = r.act > 0;
     for (int j = 0; j < kp; ++j) any_bad = any_bad || status[j] != DOT_OK;
-    CK(solve_finish(r.inner, r.o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, r.n, kp, r.st, any_bad, r.L, c->num_sms,
+    CK(solve_finish(r.inner, r.o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, c->pi.p, r.n, kp, r.st, any_bad, r.L, c->num_sms,
                     c->s));
     count(c, any_bad ? 2 : 1);
     CK(cudaMemcpyAsync(iters.data(), r.st.iters, kp * 4, cudaMemcpyDeviceToHost, c->s));
@@ -540,8 +546,8 @@ int solve_end(dot_ctx* c) {
         if (active[j] && status[j] == DOT_OK) status[j] = DOT_ENOTCONV;
     if (c->timing) {
         // algorithmic bytes of the Krylov kernels: every element of a running column read or
-        // written once per launch (stencil: p, q; update: x~, p, r~, q read, x~, r~ written;
-        // direction: r~, p read, p written), coefficients once per launch
+        // written once per launch (stencil: p, q; update: r~, q read, r~ written; direction:
+        // r~, p, x~ read, p, x~ written), coefficients once per launch
         double ci = 0.0;
         int itmax = 0;
         for (int j = 0; j < kp; ++j) {
@@ -550,8 +556,8 @@ int solve_end(dot_ctx* c) {
         }
         const double nn = (double)r.n, rs = r.mixed ? 4.0 : 8.0;
         c->kt.bytes[0] += ci * nn * 2.0 * r.ei + itmax * nn * 4.0 * rs;
-        c->kt.bytes[1] += ci * nn * 6.0 * r.ei + itmax * nn * r.ei;
-        c->kt.bytes[2] += ci * nn * 3.0 * r.ei + itmax * nn * r.ei;
+        c->kt.bytes[1] += ci * nn * 3.0 * r.ei + itmax * nn * r.ei;
+        c->kt.bytes[2] += ci * nn * 5.0 * r.ei + itmax * nn * r.ei;
     }
     float ms_solve = 0;
     cudaEventElapsedTime(&ms_solve, c->ev[1], c->ev[2]);
@@ -754,7 +760,7 @@ int dot_destroy(dot_ctx* c) {
     if (c->s) cudaStreamSynchronize(c->s);
     DevBuf* bufs[] = {&c->D, &c->mu, &c->phi, &c->wdmu, &c->p, &c->cf64, &c->dinv64, &c->cf32, &c->dinv32, &c->rpB, &c->ciB, &c->vB, &c->rpC,
                       &c->ciC, &c->vC, &c->cpC, &c->rwC, &c->vCc, &c->W, &c->V, &c->M, &c->MW, &c->P, &c->b64,
-                      &c->x64, &c->r64, &c->xi, &c->ri, &c->pi, &c->qi, &c->colbuf, &c->partA, &c->partB, &c->Tm,
+                      &c->x64, &c->r64, &c->xi, &c->ri, &c->pi, &c->qi, &c->colbuf, &c->partA, &c->partB, &c->gcount, &c->Tm,
                       &c->S, &c->Rs, &c->f, &c->gmu, &c->gp, &c->J, &c->tmp};
     for (DevBuf* b : bufs) release(*b);
     for (int t = 0; t < 4; ++t)

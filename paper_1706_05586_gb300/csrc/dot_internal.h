@@ -35,11 +35,17 @@ struct ColState {
     int* status;       // DOT_OK, DOT_ENOTCONV, DOT_EBREAKDOWN
     int* n_active;     // [1] active columns after the last finaliser
     int* n_update;     // [1] active columns waiting for an update
-    unsigned* counter; // [1] arrival counter of the last-block finaliser
+    unsigned* counter; // [1] arrival counter of the group sums (second reduction level)
     int* error;        // [1] nonzero after a bounded wait in a kernel ran out
     double2* partA;    // [grid * kp] per-block partial sums
     double* partB;     // [grid * kp]
+    double2* groupA;   // [ceil(grid / kReduceGroup) * kp] per-group sums
+    double* groupB;    // [ceil(grid / kReduceGroup) * kp]
+    unsigned* gcount;  // [ceil(grid / kReduceGroup)] arrival counters of the groups
 };
+
+// Blocks per first-level group of the per-column reductions.
+constexpr int kReduceGroup = 16;
 
 // Raw operator coefficients in one precision.
 struct OpRaw {
@@ -59,14 +65,15 @@ struct Launch {
 
 // TMA-staged stencil (stencil_tma.cu): tensor map over the p block and launch shape.
 struct TmaStencil {
-    alignas(64) unsigned char tmap[128];  // CUtensorMap
+    alignas(64) unsigned char tmap[128];     // CUtensorMap of p
+    alignas(64) unsigned char tmap_cf[128];  // CUtensorMap of the packed coefficients
     int zc = 0;                           // z planes per work item
     int grid = 0;
     size_t smem = 0;
 };
 bool tma_stencil_eligible(ElemKind inner, int nx, int ny, int kp);
-cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, int nx, int ny, int nz, int kp, int num_sms,
-                                TmaStencil* out);
+cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, const void* cf, int nx, int ny, int nz, int kp,
+                                int num_sms, TmaStencil* out);
 cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& op, const TmaStencil& t, void* q, int kp,
                                const ColState& st, cudaStream_t s);
 
@@ -88,12 +95,15 @@ cudaError_t solve_start(ElemKind inner, const OpRaw& op, const void* b64, void* 
 cudaError_t kry_step(ElemKind inner, const OpRaw& op, void* x, void* r, void* p, void* q, int64_t n, int kp,
                      const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv,
                      const TmaStencil* tma, cudaStream_t s, cudaEvent_t* ev);
-// Reliable update of the paused columns: promote x~, FP64 true residual, rescale r~.
+// Reliable update of the active columns: promote x~ (with the correction alpha p still
+// pending from the last iteration), FP64 true residual, rescale r~.
 cudaError_t solve_refresh(ElemKind inner, const OpRaw& op, const OpRaw& op64, const void* b64, void* x64, void* r64,
-                          void* x, void* r, int64_t n, int kp, const ColState& st, double rtol, int maxit,
+                          void* x, void* r, const void* p, int64_t n, int kp, const ColState& st, double rtol, int maxit,
                           const Launch& L, int num_sms, cudaStream_t s);
-// Promote every column's x~; optionally recompute every column's true residual.
-cudaError_t solve_finish(ElemKind inner, const OpRaw& op64, const void* b64, void* x64, void* r64, void* x, int64_t n,
+// Promote every column's x~ (and pending alpha p); optionally recompute every column's
+// true residual.
+cudaError_t solve_finish(ElemKind inner, const OpRaw& op64, const void* b64, void* x64, void* r64, void* x,
+                         const void* p, int64_t n,
                          int kp, const ColState& st, bool residual, const Launch& L, int num_sms, cudaStream_t s);
 cudaError_t op_apply(ElemKind ek, const OpRaw& op, const void* x, void* y, int64_t n, int kp,
                      cudaStream_t s);

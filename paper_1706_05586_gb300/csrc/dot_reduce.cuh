@@ -33,31 +33,18 @@ static __device__ __forceinline__ void column_partials(double2 a, double b, int 
     }
 }
 
-// True in every thread of the last block to finish its partial sums.
-static __device__ __forceinline__ bool arrive_last(unsigned* counter) {
-    __shared__ int am_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned t = atomicAdd(counter, 1u);
-        am_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    return am_last != 0;
-}
-
-// Totals of the per-block partial sums, computed by every thread of the last block
-// (scratch: shared memory of at least (blockDim / kp, >= 1) * kp * 24 bytes):
+// Totals of G per-block partial sums (rows of kp), computed by every thread of one
+// block (scratch: shared memory of at least (blockDim / kp, >= 1) * kp * 24 bytes):
 // tpc = blockDim / kp threads share a column, each summing a fixed strided subset of
-// the blocks with eight independent accumulators, and the subsets are combined in a
+// the rows with four independent accumulators, and the subsets are combined in a
 // fixed order, so the result does not depend on scheduling.  Returns pointers to the
-// kp totals in shared memory (valid until the block exits).
-static __device__ __noinline__ void block_sums(const double2* partA, const double* partB, int kp, void* scratch,
-                                               const double2** outA, const double** outB) {
+// kp totals in shared memory (valid until the next call or the block's exit); a
+// null input gives zeros.
+static __device__ __noinline__ void block_sums(const double2* partA, const double* partB, int kp, int G,
+                                               void* scratch, const double2** outA, const double** outB) {
     double2* sA = reinterpret_cast<double2*>(scratch);
     const int tpc = max(1, (int)blockDim.x / kp);
     double* sB = reinterpret_cast<double*>(sA + tpc * kp);
-    const int G = gridDim.x;
     for (int t = threadIdx.x; t < kp * tpc; t += blockDim.x) {
         const int cc = t % kp, q = t / kp;
         // two passes with four independent accumulators each keep the register
@@ -112,8 +99,46 @@ static __device__ __noinline__ void block_sums(const double2* partA, const doubl
     *outB = sB;
 }
 
+// Deterministic two-level reduction of the per-block partial sums (st.partA /
+// st.partB, as selected by useA / useB) after every block has written its own.
+// Blocks form groups of kReduceGroup consecutive indices; the last block of a group
+// to arrive sums that group's rows into st.groupA / st.groupB, and the last group
+// to finish sums the group rows.  Both levels add in a fixed order, so the totals do
+// not depend on which block arrives last, and no block reads more than
+// max(kReduceGroup, ceil(grid / kReduceGroup)) rows.  Returns true in every thread
+// of the one block holding the totals (*outA, *outB in shared memory); that block
+// re-arms st.counter through publish_counts, each group block its group counter.
+static __device__ __noinline__ bool reduce_columns(const ColState& st, bool useA, bool useB, int kp, void* scratch,
+                                                   const double2** outA, const double** outB) {
+    __shared__ int is_last;
+    const int G = gridDim.x;
+    const int g = blockIdx.x / kReduceGroup, ng = (G + kReduceGroup - 1) / kReduceGroup;
+    const int g0 = g * kReduceGroup, gs = min(kReduceGroup, G - g0);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&st.gcount[g], 1u) == (unsigned)(gs - 1);
+    __syncthreads();
+    if (!is_last) return false;
+    const double2* tA;
+    const double* tB;
+    block_sums(useA ? st.partA + (int64_t)g0 * kp : nullptr, useB ? st.partB + (int64_t)g0 * kp : nullptr, kp, gs,
+               scratch, &tA, &tB);
+    for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
+        if (useA) st.groupA[(int64_t)g * kp + cc] = tA[cc];
+        if (useB) st.groupB[(int64_t)g * kp + cc] = tB[cc];
+    }
+    if (threadIdx.x == 0) st.gcount[g] = 0u;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(st.counter, 1u) == (unsigned)(ng - 1);
+    __syncthreads();
+    if (!is_last) return false;
+    block_sums(useA ? st.groupA : nullptr, useB ? st.groupB : nullptr, kp, ng, scratch, outA, outB);
+    return true;
+}
+
 // Column counters written by the finalisers: active columns and columns paused for
-// a reliable update.  Also re-arms the arrival counter.
+// a reliable update.  Also re-arms the second-level arrival counter.
 static __device__ __forceinline__ void publish_counts(const ColState& st, int kp) {
     __shared__ int na, nu;
     if (threadIdx.x == 0) {

@@ -58,10 +58,9 @@ __global__ void k_start_norm(const T64* __restrict__ b, T64* __restrict__ x64, i
         x64[e] = ezero<T64>();
     }
     column_partials(make_double2(0.0, 0.0), bb, kp, slots, c, slot, nullptr, st.partB);
-    if (arrive_last(st.counter)) {
-        const double2* totA;
-        const double* totB;
-        block_sums(nullptr, st.partB, kp, smem_raw, &totA, &totB);
+    const double2* totA;
+    const double* totB;
+    if (reduce_columns(st, false, true, kp, smem_raw, &totA, &totB)) {
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             const double2 a = totA[cc];
             const double bsum = totB[cc];
@@ -74,6 +73,7 @@ __global__ void k_start_norm(const T64* __restrict__ b, T64* __restrict__ x64, i
             st.upd[cc] = 0;
             st.updates[cc] = 0;
             st.since[cc] = 0;
+            st.alpha[cc] = make_double2(0.0, 0.0);  // no correction alpha p pending
             st.status[cc] = fin ? DOT_OK : DOT_EBREAKDOWN;
             st.active[cc] = fin && bsum > 0.0;
         }
@@ -104,10 +104,9 @@ __global__ void k_start_inner(Op<T> op, const T64* __restrict__ b, T* __restrict
         rr += eabs2(rv);
     }
     column_partials(ewide(rho), (double)rr, kp, slots, c, slot, st.partA, st.partB);
-    if (arrive_last(st.counter)) {
-        const double2* totA;
-        const double* totB;
-        block_sums(st.partA, st.partB, kp, smem_raw, &totA, &totB);
+    const double2* totA;
+    const double* totB;
+    if (reduce_columns(st, true, true, kp, smem_raw, &totA, &totB)) {
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!st.active[cc]) continue;
             const double2 a = totA[cc];
@@ -230,10 +229,9 @@ __global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T
         pb[u] = 0.0;
     }
     column_partials_w<W>(pa, pb, kp, slots, c0, slot, st.partA, nullptr);
-    if (arrive_last(st.counter)) {
-        const double2* totA;
-        const double* totB;
-        block_sums(st.partA, nullptr, kp, smem_raw, &totA, &totB);
+    const double2* totA;
+    const double* totB;
+    if (reduce_columns(st, true, false, kp, smem_raw, &totA, &totB)) {
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!running(st, cc)) continue;
             const double2 a = totA[cc];
@@ -241,6 +239,7 @@ __global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T
             if (!zfinite(a) || (a.x == 0.0 && a.y == 0.0)) {
                 st.status[cc] = DOT_EBREAKDOWN;
                 st.active[cc] = 0;
+                st.alpha[cc] = make_double2(0.0, 0.0);  // the last correction is in x~ already
                 continue;
             }
             st.alpha[cc] = zdiv(st.rho[cc], a);
@@ -250,14 +249,15 @@ __global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T
     }
 }
 
-// x~ += alpha p, r~ -= alpha q, rho' = r~^T M^{-1} r~, ||r~||^2 on the running
-// columns (the others are left untouched).  Finaliser: pause the column for a
+// r~ -= alpha q, rho' = r~^T M^{-1} r~, ||r~||^2 on the running columns (the others
+// are left untouched).  The matching x~ += alpha p is deferred to the next direction
+// update, which reads p anyway (or to the refresh, if the column pauses), so this
+// pass streams two vectors instead of four.  Finaliser: pause the column for a
 // reliable update when ||r~|| reached the target, fell below delta * max||r~|| or
 // went kRefreshEvery iterations without a refresh; otherwise beta = rho' / rho.
 template <typename T>
-__global__ void __launch_bounds__(256) k_xr(Op<T> op, const T* __restrict__ p, const T* __restrict__ q,
-                                            T* __restrict__ x, T* __restrict__ r, int64_t n, int kp, int slots,
-                                            ColState st, double delta, int maxit) {
+__global__ void __launch_bounds__(256) k_r(Op<T> op, const T* __restrict__ q, T* __restrict__ r, int64_t n, int kp,
+                                           int slots, ColState st, double delta, int maxit) {
     using R = typename Elem<T>::R;
     constexpr int W = Vec16<T>::W;
     const int tpv = kp / W;
@@ -279,18 +279,16 @@ __global__ void __launch_bounds__(256) k_xr(Op<T> op, const T* __restrict__ p, c
 #pragma unroll 2
         VOXEL_LOOP(v) {
             const int64_t e = v * kp + c0;
-            const V16<T> pv = ld16(p + e), qv = ld16(q + e);
-            V16<T> xv = ld16(x + e), rv = ld16(r + e);
+            const V16<T> qv = ld16(q + e);
+            V16<T> rv = ld16(r + e);
             const T dv = op.dinv[v];
 #pragma unroll
             for (int u = 0; u < W; ++u) {
                 if (!run[u]) continue;
-                xv.e[u] = eadd(xv.e[u], emul(alpha[u], pv.e[u]));
                 rv.e[u] = esub(rv.e[u], emul(alpha[u], qv.e[u]));
                 rho[u] = eadd(rho[u], emul(rv.e[u], emul(dv, rv.e[u])));
                 rr[u] += eabs2(rv.e[u]);
             }
-            st16(x + e, xv);
             st16(r + e, rv);
         }
     }
@@ -302,10 +300,9 @@ __global__ void __launch_bounds__(256) k_xr(Op<T> op, const T* __restrict__ p, c
         pbv[u] = (double)rr[u];
     }
     column_partials_w<W>(pa, pbv, kp, slots, c0, slot, st.partA, st.partB);
-    if (arrive_last(st.counter)) {
-        const double2* totA;
-        const double* totB;
-        block_sums(st.partA, st.partB, kp, smem_raw, &totA, &totB);
+    const double2* totA;
+    const double* totB;
+    if (reduce_columns(st, true, true, kp, smem_raw, &totA, &totB)) {
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!running(st, cc)) continue;
             const double2 a = totA[cc];
@@ -345,46 +342,74 @@ __global__ void __launch_bounds__(256) k_xr(Op<T> op, const T* __restrict__ p, c
     }
 }
 
-// p = M^{-1} r~ + beta p on the running columns.
+// x~ += alpha p (the correction of the previous iteration, where one is pending),
+// then p = M^{-1} r~ + beta p, on the running columns.
 template <typename T>
-__global__ void __launch_bounds__(256) k_p(Op<T> op, const T* __restrict__ r, T* __restrict__ p, int64_t n, int kp,
-                                           int slots, ColState st) {
+__global__ void __launch_bounds__(256) k_px(Op<T> op, const T* __restrict__ r, T* __restrict__ p, T* __restrict__ x,
+                                            int64_t n, int kp, int slots, ColState st) {
     constexpr int W = Vec16<T>::W;
     const int tpv = kp / W;
     const int t = threadIdx.x % tpv, slot = threadIdx.x / tpv, c0 = t * W;
-    bool run[W];
-    bool any = false;
-    T beta[W];
+    bool run[W], corr[W];
+    bool any = false, anyx = false;
+    T beta[W], alpha[W];
 #pragma unroll
     for (int u = 0; u < W; ++u) {
         run[u] = running(st, c0 + u);
         any = any || run[u];
         beta[u] = run[u] ? enarrow<T>(st.beta[c0 + u]) : ezero<T>();
+        const double2 a = st.alpha[c0 + u];
+        corr[u] = run[u] && (a.x != 0.0 || a.y != 0.0);
+        anyx = anyx || corr[u];
+        alpha[u] = corr[u] ? enarrow<T>(a) : ezero<T>();
     }
     if (!any) return;
-    VOXEL_LOOP(v) {
-        const int64_t e = v * kp + c0;
-        const V16<T> rv = ld16(r + e);
-        V16<T> pv = ld16(p + e);
-        const T dv = op.dinv[v];
+    if (anyx) {
+        VOXEL_LOOP(v) {
+            const int64_t e = v * kp + c0;
+            const V16<T> rv = ld16(r + e);
+            V16<T> pv = ld16(p + e), xv = ld16(x + e);
+            const T dv = op.dinv[v];
 #pragma unroll
-        for (int u = 0; u < W; ++u)
-            if (run[u]) pv.e[u] = eadd(emul(dv, rv.e[u]), emul(beta[u], pv.e[u]));
-        st16(p + e, pv);
+            for (int u = 0; u < W; ++u) {
+                if (corr[u]) xv.e[u] = eadd(xv.e[u], emul(alpha[u], pv.e[u]));
+                if (run[u]) pv.e[u] = eadd(emul(dv, rv.e[u]), emul(beta[u], pv.e[u]));
+            }
+            st16(x + e, xv);
+            st16(p + e, pv);
+        }
+    } else {
+        VOXEL_LOOP(v) {
+            const int64_t e = v * kp + c0;
+            const V16<T> rv = ld16(r + e);
+            V16<T> pv = ld16(p + e);
+            const T dv = op.dinv[v];
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+                if (run[u]) pv.e[u] = eadd(emul(dv, rv.e[u]), emul(beta[u], pv.e[u]));
+            st16(p + e, pv);
+        }
     }
 }
 
 // ------------------------------------------------------------ reliable update
-// x64 += s x~, x~ = 0 on the active columns (every column when all != 0).
+// x64 += s (x~ + alpha p), x~ = 0 on the active columns (every column when all !=
+// 0), where alpha p is the correction still pending from the column's last
+// iteration (alpha = 0 when there is none).
 template <typename T64, typename T>
-__global__ void k_promote(T64* __restrict__ x64, T* __restrict__ x, int64_t n, int kp, int slots, ColState st,
-                          int all) {
+__global__ void k_promote(T64* __restrict__ x64, T* __restrict__ x, const T* __restrict__ p, int64_t n, int kp,
+                          int slots, ColState st, int all) {
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
     if (!(all || st.active[c])) return;
     const double s = st.scale[c];
+    const double2 a = st.alpha[c];
+    const bool corr = a.x != 0.0 || a.y != 0.0;
+    const T alpha = enarrow<T>(a);
     VOXEL_LOOP(v) {
         const int64_t e = v * kp + c;
-        const double2 d = ewide(x[e]);
+        T xv = x[e];
+        if (corr) xv = eadd(xv, emul(alpha, p[e]));
+        const double2 d = ewide(xv);
         x64[e] = eadd(x64[e], enarrow<T64>(make_double2(s * d.x, s * d.y)));
         x[e] = ezero<T>();
     }
@@ -412,10 +437,9 @@ __global__ void k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64
         }
     }
     column_partials(make_double2(0.0, 0.0), rr, kp, slots, c, slot, nullptr, st.partB);
-    if (arrive_last(st.counter)) {
-        const double2* totA;
-        const double* totB;
-        block_sums(nullptr, st.partB, kp, smem_raw, &totA, &totB);
+    const double2* totA;
+    const double* totB;
+    if (reduce_columns(st, false, true, kp, smem_raw, &totA, &totB)) {
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             const bool s2 = all ? true : (st.active[cc] != 0);
             if (!s2) continue;
@@ -423,6 +447,7 @@ __global__ void k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64
             const double rsum = totB[cc];
             st.rr64[cc] = rsum;
             if (all) continue;
+            st.alpha[cc] = make_double2(0.0, 0.0);  // the pending correction was promoted
             st.updates[cc] += 1;
             if (!isfinite(rsum)) {
                 st.status[cc] = DOT_EBREAKDOWN;
@@ -470,10 +495,9 @@ __global__ void k_refresh(Op<T> op, const T64* __restrict__ r64, T* __restrict__
         }
     }
     column_partials(ewide(rho), (double)rr, kp, slots, c, slot, st.partA, st.partB);
-    if (arrive_last(st.counter)) {
-        const double2* totA;
-        const double* totB;
-        block_sums(st.partA, st.partB, kp, smem_raw, &totA, &totB);
+    const double2* totA;
+    const double* totB;
+    if (reduce_columns(st, true, true, kp, smem_raw, &totA, &totB)) {
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!st.active[cc]) continue;
             const double2 a = totA[cc];
@@ -567,7 +591,7 @@ cudaError_t kry_step(ElemKind inner, const OpRaw& o, void* x, void* r, void* p, 
         Op<T> op = make_op<T>(o);
         const size_t sm = red_smem(Lv, kp);
         if (ev) record_timing(ev[0], s);
-        if (with_p) k_p<T><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, (T*)p, n, kp, Lv.slots, st);
+        if (with_p) k_px<T><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, (T*)p, (T*)x, n, kp, Lv.slots, st);
         if (ev) record_timing(ev[1], s);
         if (tma) {
             const cudaError_t e = tma_stencil_launch(inner, o, *tma, q, kp, st, s);
@@ -576,8 +600,7 @@ cudaError_t kry_step(ElemKind inner, const OpRaw& o, void* x, void* r, void* p, 
             k_pq<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)p, (T*)q, kp, Lv.slots, st);
         }
         if (ev) record_timing(ev[2], s);
-        k_xr<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)p, (const T*)q, (T*)x, (T*)r, n, kp, Lv.slots, st,
-                                                 delta, maxit);
+        k_r<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)q, (T*)r, n, kp, Lv.slots, st, delta, maxit);
         if (ev) record_timing(ev[3], s);
         (void)sizeof(T64);
     });
@@ -594,11 +617,11 @@ int vector_width(ElemKind inner) {
 }
 
 cudaError_t solve_refresh(ElemKind inner, const OpRaw& o, const OpRaw& o64, const void* b64, void* x64, void* r64,
-                          void* x, void* r, int64_t n, int kp, const ColState& st, double rtol, int maxit,
+                          void* x, void* r, const void* p, int64_t n, int kp, const ColState& st, double rtol, int maxit,
                           const Launch& L, int num_sms, cudaStream_t s) {
     (void)num_sms;
     DOT_DISPATCH2(inner, {
-        k_promote<T64, T><<<L.grid, L.threads, 0, s>>>((T64*)x64, (T*)x, n, kp, L.slots, st, 0);
+        k_promote<T64, T><<<L.grid, L.threads, 0, s>>>((T64*)x64, (T*)x, (const T*)p, n, kp, L.slots, st, 0);
         k_true_residual<T64><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<T64>(o64), (const T64*)b64,
                                                                         (const T64*)x64, (T64*)r64, n, kp, L.slots,
                                                                         st, rtol, maxit, 0);
@@ -608,11 +631,12 @@ cudaError_t solve_refresh(ElemKind inner, const OpRaw& o, const OpRaw& o64, cons
     return cudaGetLastError();
 }
 
-cudaError_t solve_finish(ElemKind inner, const OpRaw& o64, const void* b64, void* x64, void* r64, void* x, int64_t n,
+cudaError_t solve_finish(ElemKind inner, const OpRaw& o64, const void* b64, void* x64, void* r64, void* x,
+                         const void* p, int64_t n,
                          int kp, const ColState& st, bool residual, const Launch& L, int num_sms, cudaStream_t s) {
     (void)num_sms;
     DOT_DISPATCH2(inner, {
-        k_promote<T64, T><<<L.grid, L.threads, 0, s>>>((T64*)x64, (T*)x, n, kp, L.slots, st, 1);
+        k_promote<T64, T><<<L.grid, L.threads, 0, s>>>((T64*)x64, (T*)x, (const T*)p, n, kp, L.slots, st, 1);
         if (residual)
             k_true_residual<T64><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<T64>(o64), (const T64*)b64,
                                                                             (const T64*)x64, (T64*)r64, n, kp,

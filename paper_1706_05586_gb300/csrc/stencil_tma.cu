@@ -3,13 +3,16 @@
 // The 7-point operator of Sec. 2 (Eq. (PDE), Eq. (Eq:compmeas)) is applied to a
 // block of right-hand-side columns.  A CTA owns a tile of 8 x 8 cells x 32 columns
 // and marches it through a range of z planes.  Each plane of the tile, with a
-// one-cell halo in x and y, is brought into shared memory by one
-// cp.async.bulk.tensor load (4-D tensor map over [z][y][x][column]), four planes
-// deep, so every element of p crosses L2 once per plane instead of once per
-// neighbour; the z neighbours are the adjacent planes of the ring.  Out-of-range
-// halo cells are zero-filled by the copy engine (their coefficients are zero or
-// skipped).  A warp owns one tile row and a lane one column, so shared-memory reads
-// and global stores are 256-byte (complex64) or 128-byte (FP32) rows.
+// one-cell halo in x and y, is brought into shared memory by two
+// cp.async.bulk.tensor loads completing on one mbarrier: the p values (4-D tensor
+// map over [z][y][x][column]) and the packed face/diagonal coefficients of the
+// same cells (4-D map over [z][y][x][4 floats]).  Four planes are in the ring, so
+// every element of p crosses L2 once per plane instead of once per neighbour, the
+// z neighbours are the adjacent planes of the ring, and the inner loop reads only
+// shared memory.  Out-of-range halo cells are zero-filled by the copy engine, p and
+// coefficients alike, so boundary faces contribute exact zeros without branches.
+// A warp owns one tile row and a lane one column, so shared-memory reads and global
+// stores are 256-byte (complex64) or 128-byte (FP32) rows.
 //
 // Every wait on an mbarrier is bounded by a clock budget; on expiry the CTA records
 // an error code, drains its outstanding copies (again bounded) and stops issuing work.
@@ -30,6 +33,8 @@ constexpr int TX = 8, TY = 8;        // cells per tile
 constexpr int HX = TX + 2, HY = TY + 2;
 constexpr int NBUF = 4;              // planes in flight
 constexpr int THREADS = 32 * TY;     // warp w <-> tile row y = w
+constexpr int CF_BYTES = HX * HY * 16;                    // one plane of packed coefficients
+constexpr int CF_SLOT = (CF_BYTES + 127) / 128 * 128;     // its room in a ring slot
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -63,11 +68,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     }
 }
 
-// One plane of the tile: box {KC, HX, HY, 1} at (c0, i0 - 1, j0 - 1, z).
-__device__ __forceinline__ void tma_plane(const CUtensorMap* tm, void* dst, uint64_t* bar, int c0, int x, int y,
-                                          int z, uint32_t bytes) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(bar, bytes);
+__device__ __forceinline__ void tma_load4(const CUtensorMap* tm, void* dst, uint64_t* bar, int c0, int x, int y,
+                                          int z) {
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
         "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
@@ -75,28 +77,44 @@ __device__ __forceinline__ void tma_plane(const CUtensorMap* tm, void* dst, uint
         : "memory");
 }
 
+// One plane of the tile into one ring slot: p box {KC, HX, HY, 1} at (c0, i0 - 1,
+// j0 - 1, z), then the coefficient box {4, HX, HY, 1} at (0, i0 - 1, j0 - 1, z)
+// right behind it; both complete on the slot's mbarrier.
+__device__ __forceinline__ void tma_plane(const CUtensorMap* tm, const CUtensorMap* tc, unsigned char* dst,
+                                          uint32_t p_bytes, uint64_t* bar, int c0, int x, int y, int z) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, p_bytes + CF_BYTES);
+    tma_load4(tm, dst, bar, c0, x, y, z);
+    tma_load4(tc, dst + p_bytes, bar, 0, x, y, z);
+}
+
 }  // namespace
 
-// Shared memory: NBUF plane buffers, NBUF mbarriers, per-warp partials, per-CTA
-// column accumulators (kp), then the finaliser scratch reuses the plane buffers.
+// Shared memory: NBUF ring slots (a plane of p, then its coefficients), NBUF
+// mbarriers, per-CTA column accumulators (kp).  The per-warp partials of a work item
+// reuse slot 0 once its planes are consumed, and the finaliser scratch reuses the
+// ring.
 template <typename T>
-__global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ CUtensorMap tm, Op<T> op,
+__global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ CUtensorMap tm,
+                                                       const __grid_constant__ CUtensorMap tc, Op<T> op,
                                                        T* __restrict__ q, int kp, int zc_len, ColState st) {
     using R = typename Elem<T>::R;
     constexpr int PLANE = KC * HX * HY;  // elements
-    // plane buffers start on a 128-byte boundary (the copy engine's shared-memory alignment)
+    constexpr int P_BYTES = PLANE * sizeof(T);
+    constexpr int SLOT = P_BYTES + CF_SLOT;
+    static_assert(P_BYTES % 128 == 0 && TY * 32 * sizeof(double2) <= P_BYTES, "ring slot layout");
+    // ring slots start on a 128-byte boundary (the copy engine's shared-memory alignment)
     unsigned char* base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-    T* buf = reinterpret_cast<T*>(base);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)NBUF * PLANE * sizeof(T));
-    double2* wsum = reinterpret_cast<double2*>(bar + NBUF);
-    double2* acc = wsum + TY * 32;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)NBUF * SLOT);
+    double2* acc = reinterpret_cast<double2*>(bar + NBUF);  // NBUF even: 16-byte aligned
+    double2* wsum = reinterpret_cast<double2*>(base);
+    static_assert(NBUF % 2 == 0, "accumulator alignment");
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nx = op.nx, ny = op.ny, nz = op.nz, nxy = nx * ny;
+    const int nx = op.nx, ny = op.ny, nz = op.nz;
     const int tiles_x = nx / TX, tiles_y = ny / TY, tiles_c = kp / KC;
     const int zchunks = (nz + zc_len - 1) / zc_len;
     const int nitems = tiles_x * tiles_y * tiles_c * zchunks;
-    const uint32_t plane_bytes = PLANE * sizeof(T);
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < NBUF; ++b) mbar_init(&bar[b], 1);
@@ -125,9 +143,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ C
 
         // planes z0-1 .. z1 go to buffers (z - z0 + 1) mod NBUF
         auto slot = [&](int z) { return (z - z0 + 1) & (NBUF - 1); };
+        // (the barrier above also ends the previous item's reads of the partials in slot 0)
         if (threadIdx.x == 0) {
             for (int z = z0 - 1; z <= min(z0 + 1, z1); ++z)
-                tma_plane(&tm, buf + (size_t)slot(z) * PLANE, &bar[slot(z)], c0, i0 - 1, j0 - 1, z, plane_bytes);
+                tma_plane(&tm, &tc, base + (size_t)slot(z) * SLOT, P_BYTES, &bar[slot(z)], c0, i0 - 1, j0 - 1, z);
         }
         for (int z = z0 - 1; z <= min(z0 + 1, z1); ++z) pending |= 1u << slot(z);
         bool ok = true;
@@ -145,7 +164,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ C
             if (k + 2 <= z1) {
                 const int b = slot(k + 2);
                 if (threadIdx.x == 0)
-                    tma_plane(&tm, buf + (size_t)b * PLANE, &bar[b], c0, i0 - 1, j0 - 1, k + 2, plane_bytes);
+                    tma_plane(&tm, &tc, base + (size_t)b * SLOT, P_BYTES, &bar[b], c0, i0 - 1, j0 - 1, k + 2);
                 pending |= 1u << b;
             }
             {
@@ -158,25 +177,33 @@ __global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ C
             }
             failed = __syncthreads_or(!ok);
             if (failed) break;
-            const T* pm = buf + (size_t)slot(k - 1) * PLANE;
-            const T* pc = buf + (size_t)slot(k) * PLANE;
-            const T* pn = buf + (size_t)slot(k + 1) * PLANE;
+            const unsigned char* sm = base + (size_t)slot(k - 1) * SLOT;
+            const unsigned char* sc = base + (size_t)slot(k) * SLOT;
+            const T* pm = reinterpret_cast<const T*>(sm);
+            const T* pc = reinterpret_cast<const T*>(sc);
+            const T* pn = reinterpret_cast<const T*>(base + (size_t)slot(k + 1) * SLOT);
+            const Cf4<R>* cm = reinterpret_cast<const Cf4<R>*>(sm + P_BYTES);
+            const Cf4<R>* cc = reinterpret_cast<const Cf4<R>*>(sc + P_BYTES);
             const int j = j0 + warp;
             const int row = (warp + 1) * HX * KC;
+            const int crow = (warp + 1) * HX;
 #pragma unroll 2
             for (int xi = 0; xi < TX; ++xi) {
                 const int i = i0 + xi;
                 const int v = i + nx * (j + ny * k);
                 const int o = row + (xi + 1) * KC + lane;
-                const Cf4<R> cv = op.cf[v];
+                const int co = crow + xi + 1;
+                const Cf4<R> cv = cc[co];
                 const T xc = pc[o];
                 T a = escale(cv.dre, xc);
                 if (Elem<T>::cplx) a = eadd(a, emul_i(op.w, xc));
-                if (i > 0) a = esub(a, escale(op.cf[v - 1].cx, pc[o - KC]));
+                // faces to the -x, -y, -z neighbours carry that neighbour's coefficient
+                // (zero outside the grid, where p is zero as well)
+                a = esub(a, escale(cc[co - 1].cx, pc[o - KC]));
                 a = esub(a, escale(cv.cx, pc[o + KC]));
-                if (j > 0) a = esub(a, escale(op.cf[v - nx].cy, pc[o - HX * KC]));
+                a = esub(a, escale(cc[co - HX].cy, pc[o - HX * KC]));
                 a = esub(a, escale(cv.cy, pc[o + HX * KC]));
-                if (k > 0) a = esub(a, escale(op.cf[v - nxy].cz, pm[o]));
+                a = esub(a, escale(cm[co].cz, pm[o]));
                 a = esub(a, escale(cv.cz, pn[o]));
                 q[(int64_t)v * kp + c] = a;
                 pq = eadd(pq, emul(xc, a));
@@ -207,10 +234,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ C
         __syncthreads();
     }
     for (int c = threadIdx.x; c < kp; c += blockDim.x) st.partA[(int64_t)blockIdx.x * kp + c] = acc[c];
-    if (arrive_last(st.counter)) {
-        const double2* totA;
-        const double* totB;
-        block_sums(st.partA, nullptr, kp, base, &totA, &totB);
+    const double2* totA;
+    const double* totB;
+    if (reduce_columns(st, true, false, kp, base, &totA, &totB)) {
         for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
             if (!(st.active[cc] && !st.upd[cc])) continue;
             const double2 a = totA[cc];
@@ -246,12 +272,12 @@ bool tma_stencil_eligible(ElemKind inner, int nx, int ny, int kp) {
 }
 
 static size_t tma_smem(size_t es, int kp) {
-    return 128 + (size_t)NBUF * KC * HX * HY * es + NBUF * sizeof(uint64_t) + (size_t)TY * 32 * sizeof(double2) +
+    return 128 + (size_t)NBUF * ((size_t)KC * HX * HY * es + CF_SLOT) + NBUF * sizeof(uint64_t) +
            (size_t)kp * sizeof(double2);
 }
 
-cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, int nx, int ny, int nz, int kp, int num_sms,
-                                TmaStencil* out) {
+cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, const void* cf, int nx, int ny, int nz, int kp,
+                                int num_sms, TmaStencil* out) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const size_t es = inner == EK_C64 ? 8 : 4;
@@ -265,9 +291,32 @@ cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, int nx, int ny, i
                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    // packed coefficients {cx, cy, cz, dre} per cell, FP32 for both recurrence types
+    const cuuint64_t cdims[4] = {4, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t cstrides[3] = {16, (cuuint64_t)nx * 16, (cuuint64_t)nx * ny * 16};
+    const cuuint32_t cbox[4] = {4, HX, HY, 1};
+    const CUresult rc = enc(reinterpret_cast<CUtensorMap*>(out->tmap_cf), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                            const_cast<void*>(cf), cdims, cstrides, cbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (rc != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    out->smem = tma_smem(es, kp);
+    cudaError_t e;
+    int per_sm = 0;
+    if (inner == EK_C64) {
+        e = cudaFuncSetAttribute(k_pq_tma<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pq_tma<float2>, THREADS, out->smem);
+    } else {
+        e = cudaFuncSetAttribute(k_pq_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pq_tma<float>, THREADS, out->smem);
+    }
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     // z-chunk length: balance whole waves of items against the two halo planes per chunk
     const int tiles = (nx / TX) * (ny / TY) * (kp / KC);
-    const int grid_cap = 2 * num_sms;
+    const int grid_cap = per_sm * num_sms;
     int best = nz;
     double best_cost = 1e300;
     for (int zc : {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, nz}) {
@@ -284,18 +333,13 @@ cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, int nx, int ny, i
     out->zc = best;
     const long items = (long)tiles * ((nz + best - 1) / best);
     out->grid = (int)(items < grid_cap ? items : grid_cap);
-    out->smem = tma_smem(es, kp);
-    cudaError_t e;
-    if (inner == EK_C64)
-        e = cudaFuncSetAttribute(k_pq_tma<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
-    else
-        e = cudaFuncSetAttribute(k_pq_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
-    return e;
+    return cudaSuccess;
 }
 
 cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil& t, void* q, int kp,
                                const ColState& st, cudaStream_t s) {
     const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(t.tmap);
+    const CUtensorMap* tc = reinterpret_cast<const CUtensorMap*>(t.tmap_cf);
     if (inner == EK_C64) {
         Op<float2> op;
         op.cf = static_cast<const Cf4<float>*>(o.cf);
@@ -304,7 +348,7 @@ cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil&
         op.nx = o.nx;
         op.ny = o.ny;
         op.nz = o.nz;
-        k_pq_tma<float2><<<t.grid, THREADS, t.smem, s>>>(*tm, op, (float2*)q, kp, t.zc, st);
+        k_pq_tma<float2><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float2*)q, kp, t.zc, st);
     } else if (inner == EK_F32) {
         Op<float> op;
         op.cf = static_cast<const Cf4<float>*>(o.cf);
@@ -313,7 +357,7 @@ cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil&
         op.nx = o.nx;
         op.ny = o.ny;
         op.nz = o.nz;
-        k_pq_tma<float><<<t.grid, THREADS, t.smem, s>>>(*tm, op, (float*)q, kp, t.zc, st);
+        k_pq_tma<float><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st);
     } else {
         return cudaErrorInvalidValue;
     }
