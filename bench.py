@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="let the library time its launch variants on the first solve and keep the fastest")
     ap.add_argument("--api", choices=("abi", "autograd"), default="abi",
                     help="abi: dot_set_pals_dev + dot_gradient per step; autograd: forward and backward of "
                          "the torch.autograd.Function per step")
@@ -215,6 +217,7 @@ def run_ours(args):
     ctx = D.dot_create(local)
     D.dot_set_stream(ctx, stream.cuda_stream)
     Dfield, M = setup_problem(D, ctx, wl, inp, args.precision, args.rtol, log)
+    D.dot_set_launch_options(ctx, True, args.autotune)
     ps = p_sequence(inp, args.warmup + args.steps)
     p_dev = torch.tensor(np.stack(ps), dtype=torch.float64, device=f"cuda:{local}")
     pals = (synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
@@ -266,7 +269,8 @@ def run_ours(args):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     kt = D.dot_get_kernel_timing(ctx)
-    launches = D.dot_get_stats(ctx)["kernel_launches"] - launches0
+    last_stats = D.dot_get_stats(ctx)
+    launches = last_stats["kernel_launches"] - launches0
     dev = f"cuda:{local}"
     ms_max = max_over_ranks(ms, dev)
     value = whole_job_rate(args.steps, ms / 1e3, ws, dev)
@@ -300,7 +304,10 @@ def run_ours(args):
                       "krylov_iters_per_step": [it[0] for it in iters], "outer_steps": [it[1] for it in iters],
                       "relres_max": max(it[2] for it in iters),
                       "l2": "inputs larger than L2 (each Krylov block vector >= 512 MiB)",
-                      "parallelism": f"replicas x{ws}", "api": args.api},
+                      "parallelism": f"replicas x{ws}", "api": args.api,
+                      "launch": {"graphs": True, "autotune": bool(args.autotune),
+                                 "tma_stencil": bool(last_stats["tuned_tma"]) if args.autotune else None,
+                                 "blocks_per_sm": last_stats["tuned_blocks_per_sm"] if args.autotune else 8}},
            "clocks": clk, "gpu_launches": int(launches), "roofline": roofline}
 
     # plain FP64 GPU path at the last p: its throughput at the same stopping rule, and a
@@ -482,8 +489,16 @@ def run_batch(args):
         torch.cuda.synchronize()
         return D.dot_gradient_batch(hs, ngs)
 
+    # the first warm-up evaluates the members one at a time, so that each autotunes its
+    # launches on an otherwise idle GPU; the later ones run as the timed batch does
     for k in range(args.warmup):
-        step(k)
+        if k == 0:
+            for h, pd, pals, wl in zip(hs, pdev, pals_all, members):
+                D.dot_set_pals_dev(h, wl.m0, pd[k].data_ptr(), *pals)
+                torch.cuda.synchronize()
+                D.dot_gradient(h, wl.np_)
+        else:
+            step(k)
         log(f"warmup {k}: iters {[D.dot_get_stats(h)['iters_max'] for h in hs]}")
     for h in hs:
         D.dot_set_kernel_timing(h, 1)
@@ -501,8 +516,11 @@ def run_batch(args):
     kts = [D.dot_get_kernel_timing(h) for h in hs]
     kt = {nm: {q: sum(t[nm][q] for t in kts) for q in ("launches", "ms", "bytes")} for nm in kts[0]}
     peaks, peak_kind = measured_peaks()
-    dom = max(kt, key=lambda nm: kt[nm]["ms"])
-    achieved = kt[dom]["bytes"] / (kt[dom]["ms"] * 1e-3) / 1e9 if kt[dom]["ms"] else 0.0
+    # the members' kernels overlap on their streams, so per-kernel event times include
+    # the other members' work: report the aggregate algorithmic bytes of all Krylov
+    # kernels of all members over the wall time of the timed steps instead
+    total_bytes = sum(kt[nm]["bytes"] for nm in kt)
+    achieved = total_bytes / te / 1e9
     evals = args.steps * len(members)
     out = {"metric": "misfit+gradient evals/s, 8 inversions with uneven grids (23.3M cells in all)",
            "value": round(evals / te, 4), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -514,10 +532,11 @@ def run_batch(args):
                       "tuned": [[st["tuned_tma"], st["tuned_blocks_per_sm"]] for st in stats],
                       "timing": "host clock around device-synchronised steps (members on their own streams)"},
            "clocks": clk, "gpu_launches": int(sum(st["kernel_launches"] for st in stats) - launches0),
-           "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                        "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
-                        "kernels": {nm: {"launches": kt[nm]["launches"], "ms": round(kt[nm]["ms"], 2)}
-                                    for nm in kt}}}
+           "roofline": {"bound": "hbm", "kernel": "all Krylov kernels of the 8 members (aggregate over the step)",
+                        "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                        "algorithmic_bytes_per_step": total_bytes / args.steps,
+                        "kernels": {nm: {"launches": kt[nm]["launches"]} for nm in kt}}}
     for h in hs:
         D.dot_destroy(h)
     print(json.dumps(out), flush=True)

@@ -67,6 +67,7 @@ struct Launch {
 struct TmaStencil {
     alignas(64) unsigned char tmap[128];     // CUtensorMap of p
     alignas(64) unsigned char tmap_cf[128];  // CUtensorMap of the packed coefficients
+    int kc = 32;                          // columns per tile (32, or 16)
     int zc = 0;                           // z planes per work item
     int grid = 0;
     size_t smem = 0;

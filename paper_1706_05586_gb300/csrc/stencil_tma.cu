@@ -1,7 +1,8 @@
 // TMA-staged stencil q = A p with the per-column dot products p^T q (sm_103a).
 //
 // The 7-point operator of Sec. 2 (Eq. (PDE), Eq. (Eq:compmeas)) is applied to a
-// block of right-hand-side columns.  A CTA owns a tile of 8 x 8 cells x 32 columns
+// block of right-hand-side columns.  A CTA owns a tile of 8 x 8 cells x KC columns
+// (KC = 32, or 16 when the block width is an odd multiple of 16)
 // and marches it through a range of z planes.  Each plane of the tile, with a
 // one-cell halo in x and y, is brought into shared memory by two
 // cp.async.bulk.tensor loads completing on one mbarrier: the p values (4-D tensor
@@ -11,8 +12,9 @@
 // z neighbours are the adjacent planes of the ring, and the inner loop reads only
 // shared memory.  Out-of-range halo cells are zero-filled by the copy engine, p and
 // coefficients alike, so boundary faces contribute exact zeros without branches.
-// A warp owns one tile row and a lane one column, so shared-memory reads and global
-// stores are 256-byte (complex64) or 128-byte (FP32) rows.
+// A warp owns one tile row; with KC = 32 a lane owns one column, with KC = 16 a
+// half-warp owns one cell, so every shared-memory read and global store of a warp is
+// one contiguous 256-byte (complex64) or 128-byte (FP32) run.
 //
 // Every wait on an mbarrier is bounded by a clock budget; on expiry the CTA records
 // an error code, drains its outstanding copies (again bounded) and stops issuing work.
@@ -28,7 +30,6 @@ namespace dotk {
 
 namespace {
 
-constexpr int KC = 32;               // columns per tile
 constexpr int TX = 8, TY = 8;        // cells per tile
 constexpr int HX = TX + 2, HY = TY + 2;
 constexpr int NBUF = 4;              // planes in flight
@@ -94,8 +95,8 @@ __device__ __forceinline__ void tma_plane(const CUtensorMap* tm, const CUtensorM
 // mbarriers, per-CTA column accumulators (kp).  The per-warp partials of a work item
 // reuse slot 0 once its planes are consumed, and the finaliser scratch reuses the
 // ring.
-template <typename T>
-__global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ CUtensorMap tm,
+template <typename T, int KC>
+__global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __grid_constant__ CUtensorMap tm,
                                                        const __grid_constant__ CUtensorMap tc, Op<T> op,
                                                        T* __restrict__ q, int kp, int zc_len, ColState st) {
     using R = typename Elem<T>::R;
@@ -109,8 +110,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ C
     double2* acc = reinterpret_cast<double2*>(bar + NBUF);  // NBUF even: 16-byte aligned
     double2* wsum = reinterpret_cast<double2*>(base);
     static_assert(NBUF % 2 == 0, "accumulator alignment");
+    static_assert(KC == 16 || KC == 32, "column tile");
+    constexpr int XS = 32 / KC;  // cells per warp instruction
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = lane % KC, xsub = lane / KC;
     const int nx = op.nx, ny = op.ny, nz = op.nz;
     const int tiles_x = nx / TX, tiles_y = ny / TY, tiles_c = kp / KC;
     const int zchunks = (nz + zc_len - 1) / zc_len;
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ C
         const int zci = rem / tiles_c;
         const int i0 = txi * TX, j0 = tyi * TY, c0 = cci * KC;
         const int z0 = zci * zc_len, z1 = min(z0 + zc_len, nz);
-        const int c = c0 + lane;
+        const int c = c0 + col;
         const bool run = st.active[c] && !st.upd[c];
         if (!__syncthreads_or(run)) continue;
 
@@ -188,10 +192,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ C
             const int row = (warp + 1) * HX * KC;
             const int crow = (warp + 1) * HX;
 #pragma unroll 2
-            for (int xi = 0; xi < TX; ++xi) {
+            for (int xi = xsub; xi < TX; xi += XS) {
                 const int i = i0 + xi;
                 const int v = i + nx * (j + ny * k);
-                const int o = row + (xi + 1) * KC + lane;
+                const int o = row + (xi + 1) * KC + col;
                 const int co = crow + xi + 1;
                 const Cf4<R> cv = cc[co];
                 const T xc = pc[o];
@@ -211,17 +215,19 @@ __global__ void __launch_bounds__(THREADS, 2) k_pq_tma(const __grid_constant__ C
             __syncthreads();  // plane k-1's buffer is refilled in the next iteration
         }
         if (failed) break;
-        // fold this item's per-lane sums into the CTA's column accumulators in warp order
+        // fold this item's per-lane sums into the CTA's column accumulators in a fixed
+        // order (warp, then half-warp)
         wsum[warp * 32 + lane] = ewide(pq);
         __syncthreads();
-        if (warp == 0) {
+        if (threadIdx.x < KC) {
             double2 s = make_double2(0.0, 0.0);
-            for (int w = 0; w < TY; ++w) {
-                s.x += wsum[w * 32 + lane].x;
-                s.y += wsum[w * 32 + lane].y;
-            }
-            acc[c].x += s.x;
-            acc[c].y += s.y;
+            for (int w = 0; w < TY; ++w)
+                for (int h = 0; h < XS; ++h) {
+                    s.x += wsum[w * 32 + h * KC + threadIdx.x].x;
+                    s.y += wsum[w * 32 + h * KC + threadIdx.x].y;
+                }
+            acc[c0 + threadIdx.x].x += s.x;
+            acc[c0 + threadIdx.x].y += s.y;
         }
         __syncthreads();
     }
@@ -267,13 +273,21 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 bool tma_stencil_eligible(ElemKind inner, int nx, int ny, int kp) {
-    return (inner == EK_C64 || inner == EK_F32) && nx % TX == 0 && ny % TY == 0 && kp % KC == 0 && kp <= 1024 &&
+    return (inner == EK_C64 || inner == EK_F32) && nx % TX == 0 && ny % TY == 0 && kp % 16 == 0 && kp <= 1024 &&
            encode_fn() != nullptr;
 }
 
-static size_t tma_smem(size_t es, int kp) {
-    return 128 + (size_t)NBUF * ((size_t)KC * HX * HY * es + CF_SLOT) + NBUF * sizeof(uint64_t) +
+static size_t tma_smem(size_t es, int kc, int kp) {
+    return 128 + (size_t)NBUF * ((size_t)kc * HX * HY * es + CF_SLOT) + NBUF * sizeof(uint64_t) +
            (size_t)kp * sizeof(double2);
+}
+
+// Shared-memory opt-in and resident blocks per SM of one instantiation.
+template <typename T, int KC>
+static cudaError_t tma_configure(size_t smem, int* per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_pq_tma<T, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pq_tma<T, KC>, THREADS, smem);
+    return e;
 }
 
 cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, const void* cf, int nx, int ny, int nz, int kp,
@@ -281,9 +295,10 @@ cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, const void* cf, i
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const size_t es = inner == EK_C64 ? 8 : 4;
+    const int kc = kp % 32 == 0 ? 32 : 16;
     const cuuint64_t dims[4] = {(cuuint64_t)kp, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     const cuuint64_t strides[3] = {(cuuint64_t)kp * es, (cuuint64_t)kp * nx * es, (cuuint64_t)kp * nx * ny * es};
-    const cuuint32_t box[4] = {KC, HX, HY, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)kc, HX, HY, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUresult r = enc(reinterpret_cast<CUtensorMap*>(out->tmap), inner == EK_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64
                                                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -300,22 +315,18 @@ cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, const void* cf, i
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (rc != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    out->smem = tma_smem(es, kp);
-    cudaError_t e;
+    out->kc = kc;
+    out->smem = tma_smem(es, kc, kp);
     int per_sm = 0;
-    if (inner == EK_C64) {
-        e = cudaFuncSetAttribute(k_pq_tma<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pq_tma<float2>, THREADS, out->smem);
-    } else {
-        e = cudaFuncSetAttribute(k_pq_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pq_tma<float>, THREADS, out->smem);
-    }
+    cudaError_t e;
+    if (inner == EK_C64)
+        e = kc == 32 ? tma_configure<float2, 32>(out->smem, &per_sm) : tma_configure<float2, 16>(out->smem, &per_sm);
+    else
+        e = kc == 32 ? tma_configure<float, 32>(out->smem, &per_sm) : tma_configure<float, 16>(out->smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     // z-chunk length: balance whole waves of items against the two halo planes per chunk
-    const int tiles = (nx / TX) * (ny / TY) * (kp / KC);
+    const int tiles = (nx / TX) * (ny / TY) * (kp / kc);
     const int grid_cap = per_sm * num_sms;
     int best = nz;
     double best_cost = 1e300;
@@ -348,7 +359,10 @@ cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil&
         op.nx = o.nx;
         op.ny = o.ny;
         op.nz = o.nz;
-        k_pq_tma<float2><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float2*)q, kp, t.zc, st);
+        if (t.kc == 32)
+            k_pq_tma<float2, 32><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float2*)q, kp, t.zc, st);
+        else
+            k_pq_tma<float2, 16><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float2*)q, kp, t.zc, st);
     } else if (inner == EK_F32) {
         Op<float> op;
         op.cf = static_cast<const Cf4<float>*>(o.cf);
@@ -357,7 +371,10 @@ cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil&
         op.nx = o.nx;
         op.ny = o.ny;
         op.nz = o.nz;
-        k_pq_tma<float><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st);
+        if (t.kc == 32)
+            k_pq_tma<float, 32><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st);
+        else
+            k_pq_tma<float, 16><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st);
     } else {
         return cudaErrorInvalidValue;
     }

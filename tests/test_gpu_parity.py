@@ -44,6 +44,11 @@ CASES = {
                                               ls=16, ld=16, m0=5, sampling="gaussian", seed_index=65),
     "real_16x16x9_k32": synth.small_workload(16, 16, 9, 0.3, src_grid=(4, 4), det_grid=(4, 4), ls=16, ld=16,
                                              m0=4, sampling="gaussian", seed_index=66),
+    # block widths 48 and 16 (odd multiples of 16): the TMA stencil with 16-column tiles
+    "cplx_16x24x8_k48": synth.small_workload(16, 24, 8, 0.3, omega_nu=0.4, src_grid=(5, 5), det_grid=(5, 5),
+                                             ls=24, ld=24, m0=5, sampling="gaussian", seed_index=67),
+    "real_24x8x7_k16": synth.small_workload(24, 8, 7, 0.3, src_grid=(3, 3), det_grid=(3, 3), ls=8, ld=8,
+                                            m0=4, sampling="gaussian", seed_index=68),
     # the 100 MHz frequency on a 24x20x12 grid
     "cplx_24x20x12_100MHz": synth.small_workload(24, 20, 12, 0.25, omega_nu=synth.OMEGA_NU_100MHZ, src_grid=(3, 3),
                                                  det_grid=(3, 3), ls=4, ld=4, m0=8, sampling="gaussian",
@@ -245,7 +250,7 @@ def test_forward_model_all_sources(name, ctx):
     assert misfit_err(f, out) <= 1e-10
 
 
-@pytest.mark.parametrize("name", ["cplx_24x16x10_k32", "real_16x16x9_k32"])
+@pytest.mark.parametrize("name", ["cplx_24x16x10_k32", "real_16x16x9_k32", "cplx_16x24x8_k48", "real_24x8x7_k16"])
 def test_tma_stencil_matches_direct_load_kernel(name, ctx):
     """The TMA-staged stencil and the direct-load stencil give the same solve to rounding."""
     pb, ref = _case(name)
