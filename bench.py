@@ -306,8 +306,8 @@ def run_ours(args):
                       "l2": "inputs larger than L2 (each Krylov block vector >= 512 MiB)",
                       "parallelism": f"replicas x{ws}", "api": args.api,
                       "launch": {"graphs": True, "autotune": bool(args.autotune),
-                                 "tma_stencil": bool(last_stats["tuned_tma"]) if args.autotune else None,
-                                 "blocks_per_sm": last_stats["tuned_blocks_per_sm"] if args.autotune else 8}},
+                                 "tma_stencil": last_stats["tuned_tma"] == 1,
+                                 "blocks_per_sm": last_stats["tuned_blocks_per_sm"]}},
            "clocks": clk, "gpu_launches": int(launches), "roofline": roofline}
 
     # plain FP64 GPU path at the last p: its throughput at the same stopping rule, and a

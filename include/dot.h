@@ -79,8 +79,8 @@ typedef struct dot_stats {
     double  ms_solve;        /* last: block Krylov solve                              */
     double  ms_post;         /* last: restriction, misfit, sensitivity, chain rule    */
     int64_t kernel_launches; /* cumulative number of this library's kernel launches   */
-    int32_t tuned_tma;       /* autotuned stencil path (1 TMA, 0 direct, -1 not tuned) */
-    int32_t tuned_blocks_per_sm; /* autotuned blocks per SM of the vector kernels (-1) */
+    int32_t tuned_tma;       /* stencil path of the last solve, autotuned or default (1 TMA, 0 direct, -1 no solve yet) */
+    int32_t tuned_blocks_per_sm; /* blocks per SM of the vector kernels in the last solve (-1 no solve yet) */
 } dot_stats;
 
 /* Per-kernel device time of the Krylov kernels, accumulated while timing is on.

@@ -182,6 +182,7 @@ struct dot_ctx {
     bool use_graphs = true;
     bool autotune = false;
     TunedChoice tuned;
+    Tuning last_cfg{false, -1};  // launch configuration of the last solve (blocks_per_sm -1: none yet)
     cudaEvent_t bev[2] = {nullptr, nullptr};
 
     // kernel timing (dot_set_kernel_timing)
@@ -393,7 +394,7 @@ int solve_begin(dot_ctx* c, int kp, int kr) {
     r.delta = r.mixed ? c->delta : 0.0;
     r.maxit = c->maxit > 0 ? c->maxit : 10 * (c->nx + c->ny + c->nz);
     const bool tma_ok = tma_stencil_eligible(r.inner, c->nx, c->ny, kp);
-    Tuning base{c->use_tma && tma_ok, 8};
+    Tuning base{c->use_tma && tma_ok, 4};  // four 256-thread blocks per SM: one wave, ample bytes in flight
     if (c->autotune) {
         const bool have = c->tuned.valid && c->tuned.n == r.n && c->tuned.kp == kp && c->tuned.inner == (int)r.inner;
         if (have) {
@@ -524,6 +525,7 @@ int solve_poll(dot_ctx* c) {
 int solve_end(dot_ctx* c) {
     SolveRun& r = c->run;
     const int kp = r.kp;
+    c->last_cfg = r.cfg;
     std::vector<int> iters(kp), updates(kp), status(kp), active(kp);
     std::vector<double> rr(kp), bb(kp);
     CK(cudaMemcpyAsync(status.data(), r.st.status, kp * 4, cudaMemcpyDeviceToHost, c->s));
@@ -1192,8 +1194,8 @@ int dot_get_fields(dot_ctx* c, double* U, double* Z) {
 int dot_get_stats(dot_ctx* c, dot_stats* out) {
     if (!c || !out) return fail(DOT_EINVAL, "null argument");
     *out = c->stats;
-    out->tuned_tma = c->tuned.valid ? (c->tuned.tma ? 1 : 0) : -1;
-    out->tuned_blocks_per_sm = c->tuned.valid ? c->tuned.blocks_per_sm : -1;
+    out->tuned_tma = c->last_cfg.blocks_per_sm < 0 ? -1 : (c->last_cfg.tma ? 1 : 0);
+    out->tuned_blocks_per_sm = c->last_cfg.blocks_per_sm;
     return DOT_OK;
 }
 

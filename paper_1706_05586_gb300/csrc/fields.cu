@@ -3,6 +3,7 @@
 // PaLS chain rule.  All reductions are deterministic (fixed-order block sums).
 #include "dot_kernels.cuh"
 #include "dot_internal.h"
+#include "dfloat.cuh"
 #include "dot.h"
 
 namespace dotk {
@@ -331,39 +332,75 @@ cudaError_t restriction_misfit(bool cplx, const void* X, int kp, int ls, const i
 // g_mu[v] = -2 Re sum_{i,l} conj(R_s[l,i]) Z_l[v] U_i[v]: the gradient of
 // ||R_s||^2 through J_mu[(l,i), v] = -Z_l[v] U_i[v] (Eq. (Jacobiancomp) with
 // dA/dmu_v = e_v e_v^T, sampled as in Eq. (Jacobian kth column)).
+//
+// l_s l_d complex products per cell: the sums run in double-float arithmetic on the
+// FP32 pipe (inputs rounded from FP64 to about 48 bits, accumulation error of the same
+// order relative to sum |R_s||Z||U|) instead of on the FP64 pipe.  One thread per cell;
+// y_i = sum_l conj(R_s[l,i]) Z_l for a chunk of IC sources at a time keeps the
+// accumulators in registers; R_s is split once per block into shared memory.
+constexpr int kGmuChunk = 8;
+constexpr int kGmuSmemEntries = 3072;  // 48 KiB of (re.hi, re.lo, im.hi, im.lo)
+
+__device__ __forceinline__ float4 df_split2(double2 r) {
+    const dfloat a = df_from(r.x), b = df_from(r.y);
+    return make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
 template <typename T>
-__global__ void k_gmu(const T* __restrict__ X, int64_t n, int kp, int ls, int ld, const double2* __restrict__ Rs,
-                      double* __restrict__ gmu) {
-    extern __shared__ double2 sR[];
+__global__ void __launch_bounds__(128) k_gmu(const T* __restrict__ X, int64_t n, int kp, int ls, int ld,
+                                             const double2* __restrict__ Rs, double* __restrict__ gmu) {
+    constexpr bool C = Elem<T>::cplx;
+    constexpr int IC = kGmuChunk;
+    extern __shared__ float4 sRf[];
     const int nr = ls * ld;
-    const bool in_smem = nr <= 2048;
+    const bool in_smem = nr <= kGmuSmemEntries;
     if (in_smem)
-        for (int t = threadIdx.x; t < nr; t += blockDim.x) sR[t] = Rs[t];
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) sRf[t] = df_split2(Rs[t]);
     __syncthreads();
-    const double2* R = in_smem ? sR : Rs;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const T* row = X + v * kp;
-        double g = 0.0;
-        for (int i = 0; i < ls; ++i) {
-            const double2 u = ewide(row[i]);
-            double2 y = make_double2(0.0, 0.0);
+        dfloat g = df_zero();
+        for (int i0 = 0; i0 < ls; i0 += IC) {
+            const int nc = min(IC, ls - i0);
+            dfloat yr[IC], yi[IC];
+#pragma unroll
+            for (int c = 0; c < IC; ++c) yr[c] = yi[c] = df_zero();
             for (int l = 0; l < ld; ++l) {
                 const double2 z = ewide(row[ls + l]);
-                const double2 r = R[l + ld * i];
-                // conj(r) * z
-                y.x += r.x * z.x + r.y * z.y;
-                y.y += r.x * z.y - r.y * z.x;
+                const dfloat zr = df_from(z.x);
+                const dfloat zi = C ? df_from(z.y) : df_zero();
+#pragma unroll
+                for (int c = 0; c < IC; ++c) {
+                    if (c >= nc) break;
+                    const int e = l + ld * (i0 + c);
+                    const float4 r = in_smem ? sRf[e] : df_split2(Rs[e]);
+                    const dfloat rr{r.x, r.y};
+                    // conj(r) z = (rr zr + ri zi) + i (rr zi - ri zr)
+                    yr[c] = df_fma(rr, zr, yr[c]);
+                    if (C) {
+                        const dfloat ri{r.z, r.w};
+                        yr[c] = df_fma(ri, zi, yr[c]);
+                        yi[c] = df_fma(rr, zi, yi[c]);
+                        yi[c] = df_fma(df_neg(ri), zr, yi[c]);
+                    }
+                }
             }
-            g += y.x * u.x - y.y * u.y;
+#pragma unroll
+            for (int c = 0; c < IC; ++c) {
+                if (c >= nc) break;
+                const double2 u = ewide(row[i0 + c]);
+                g = df_fma(yr[c], df_from(u.x), g);
+                if (C) g = df_fma(df_neg(yi[c]), df_from(u.y), g);
+            }
         }
-        gmu[v] = -2.0 * g;
+        gmu[v] = -2.0 * df_to_double(g);
     }
 }
 
 cudaError_t sensitivity_gmu(bool cplx, const void* X, int64_t n, int kp, int ls, int ld, const double* Rs, double* gmu,
                             cudaStream_t s) {
     const int nr = ls * ld;
-    const size_t sm = nr <= 2048 ? (size_t)nr * sizeof(double2) : 0;
+    const size_t sm = nr <= kGmuSmemEntries ? (size_t)nr * sizeof(float4) : 0;
     const int g = grid_for(n, 128);
     if (cplx)
         k_gmu<double2><<<g, 128, sm, s>>>((const double2*)X, n, kp, ls, ld, (const double2*)Rs, gmu);

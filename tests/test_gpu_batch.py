@@ -126,3 +126,14 @@ def test_batch_with_kernel_timing(problems):
     for i, pb in enumerate(problems):
         f1, g1, _ = _single(pb, D.PREC_MIXED, 1e-12)
         assert f[i] == f1 and np.array_equal(gs[i], g1)
+
+
+def test_stats_report_the_launch_configuration(problems):
+    # without the autotuner every solve runs 4 blocks per SM and, where the shape allows
+    # it (8-aligned x, y and a block width that is a multiple of 16), the TMA stencil
+    for pb in problems:
+        st = _single(pb, D.PREC_MIXED, 1e-12)[2]
+        kp = -(-(pb.wl.ls + pb.wl.ld) // 4) * 4
+        tma_ok = pb.wl.nx % 8 == 0 and pb.wl.ny % 8 == 0 and kp % 16 == 0
+        assert st["tuned_blocks_per_sm"] == 4
+        assert st["tuned_tma"] == (1 if tma_ok else 0)
