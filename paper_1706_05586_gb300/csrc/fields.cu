@@ -29,37 +29,97 @@ __device__ __forceinline__ double wendland_prime(double r) {
 // phi(x_v) = sum_j alpha_j psi(sqrt(beta_j^2 |x_v - chi_j|^2 + gamma^2)),
 // mu = mu_out + (mu_in - mu_out) H_eps(phi - c), wdmu = (mu_in - mu_out) H_eps'(phi - c),
 // with the C^1 sine ramp H_eps (Eq. (absorption const); the ramp is this library's reading).
-__global__ void k_pals_eval(const double* __restrict__ p, int m0, double mu_in, double mu_out, double c, double eps,
-                            double gamma, int nx, int ny, int nz, double h, double* __restrict__ phi_out,
-                            double* __restrict__ mu_out_arr, double* __restrict__ wdmu) {
+//
+// A block owns a tile of 8 x 8 x 4 cells.  It first lists, in increasing j, the RBFs
+// whose support (r < 1) can reach a cell centre of the tile (a conservative test on
+// the distance from chi_j to the tile's box of centres), then sums only those.  The
+// skipped terms are exact zeros of the sum, and the kept ones are added in the same
+// order as a loop over all j, so phi is the same to the last bit.
+constexpr int kPalsTx = 8, kPalsTy = 8, kPalsTz = 4;
+constexpr int kPalsCullMax = 4096;  // RBFs that the tile list can hold; more: no culling
+
+__global__ void __launch_bounds__(256) k_pals_eval(const double* __restrict__ p, int m0, double mu_in, double mu_out,
+                                                   double c, double eps, double gamma, int nx, int ny, int nz, double h,
+                                                   double* __restrict__ phi_out, double* __restrict__ mu_out_arr,
+                                                   double* __restrict__ wdmu) {
     constexpr int CH = 128;
     __shared__ double sp[5 * CH];
-    const int64_t n = (int64_t)nx * ny * nz;
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double x = 0, y = 0, z = 0;
-    if (v < n) {
-        x = ((double)(v % nx) + 0.5) * h;
-        y = ((double)((v / nx) % ny) + 0.5) * h;
-        z = ((double)(v / ((int64_t)nx * ny)) + 0.5) * h;
-    }
+    __shared__ int slist[kPalsCullMax];
+    __shared__ unsigned smask[kPalsCullMax / 32];
+    __shared__ int soff[kPalsCullMax / 32];
+    __shared__ int scount;
+    const int tiles_x = (nx + kPalsTx - 1) / kPalsTx, tiles_y = (ny + kPalsTy - 1) / kPalsTy;
+    const int tb = blockIdx.x;
+    const int ti = tb % tiles_x, tj = (tb / tiles_x) % tiles_y, tk = tb / (tiles_x * tiles_y);
+    const int i = ti * kPalsTx + threadIdx.x % kPalsTx;
+    const int j = tj * kPalsTy + (threadIdx.x / kPalsTx) % kPalsTy;
+    const int k = tk * kPalsTz + threadIdx.x / (kPalsTx * kPalsTy);
+    const bool in = i < nx && j < ny && k < nz;
+    const double x = (i + 0.5) * h, y = (j + 0.5) * h, z = (k + 0.5) * h;
     const double g2 = gamma * gamma;
+    const bool cull = m0 <= kPalsCullMax;
+    int cnt = m0;
+    if (cull) {
+        // box of the tile's cell centres (clipped to the grid)
+        const double xlo = (ti * kPalsTx + 0.5) * h, xhi = (min(ti * kPalsTx + kPalsTx, nx) - 0.5) * h;
+        const double ylo = (tj * kPalsTy + 0.5) * h, yhi = (min(tj * kPalsTy + kPalsTy, ny) - 0.5) * h;
+        const double zlo = (tk * kPalsTz + 0.5) * h, zhi = (min(tk * kPalsTz + kPalsTz, nz) - 0.5) * h;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        const int nch = (m0 + 31) / 32;
+        for (int ch = warp; ch < nch; ch += nwarps) {
+            const int jj = ch * 32 + lane;
+            bool keep = false;
+            if (jj < m0) {
+                const double be = p[5 * jj + 1];
+                const double cx = p[5 * jj + 2], cy = p[5 * jj + 3], cz = p[5 * jj + 4];
+                const double dx = fmax(0.0, fmax(xlo - cx, cx - xhi));
+                const double dy = fmax(0.0, fmax(ylo - cy, cy - yhi));
+                const double dz = fmax(0.0, fmax(zlo - cz, cz - zhi));
+                // drop only when every centre of the tile is certainly outside r < 1
+                // (margin for the rounding of the per-cell distance)
+                keep = !(be * be * (dx * dx + dy * dy + dz * dz) * (1.0 - 1e-12) + g2 >= 1.0);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) smask[ch] = m;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int ch = 0; ch < nch; ++ch) {
+                soff[ch] = run;
+                run += __popc(smask[ch]);
+            }
+            scount = run;
+        }
+        __syncthreads();
+        for (int ch = warp; ch < nch; ch += nwarps) {
+            const unsigned m = smask[ch];
+            if (m & (1u << lane)) slist[soff[ch] + __popc(m & ((1u << lane) - 1u))] = ch * 32 + lane;
+        }
+        __syncthreads();
+        cnt = scount;
+    }
     double phi = 0.0;
-    for (int j0 = 0; j0 < m0; j0 += CH) {
-        const int cnt = min(CH, m0 - j0);
+    for (int q0 = 0; q0 < cnt; q0 += CH) {
+        const int nq = min(CH, cnt - q0);
         __syncthreads();
-        for (int t = threadIdx.x; t < 5 * cnt; t += blockDim.x) sp[t] = p[5 * j0 + t];
+        for (int t = threadIdx.x; t < 5 * nq; t += blockDim.x) {
+            const int jj = cull ? slist[q0 + t / 5] : q0 + t / 5;
+            sp[t] = p[5 * jj + t % 5];
+        }
         __syncthreads();
-        if (v < n) {
-            for (int j = 0; j < cnt; ++j) {
-                const double a = sp[5 * j], be = sp[5 * j + 1];
-                const double dx = x - sp[5 * j + 2], dy = y - sp[5 * j + 3], dz = z - sp[5 * j + 4];
+        if (in) {
+            for (int q = 0; q < nq; ++q) {
+                const double a = sp[5 * q], be = sp[5 * q + 1];
+                const double dx = x - sp[5 * q + 2], dy = y - sp[5 * q + 3], dz = z - sp[5 * q + 4];
                 const double d2 = dx * dx + dy * dy + dz * dz;
                 const double r2 = be * be * d2 + g2;
                 if (r2 < 1.0) phi += a * wendland(sqrt(r2));
             }
         }
     }
-    if (v < n) {
+    if (in) {
+        const int64_t v = i + (int64_t)nx * (j + (int64_t)ny * k);
         const double t = phi - c;
         double H, dH;
         if (t < -eps) {
@@ -80,10 +140,10 @@ __global__ void k_pals_eval(const double* __restrict__ p, int m0, double mu_in, 
 
 cudaError_t pals_eval(const double* p, int m0, double mu_in, double mu_out, double c, double eps, double gamma,
                       int nx, int ny, int nz, double h, double* phi, double* mu, double* wdmu, cudaStream_t s) {
-    const int64_t n = (int64_t)nx * ny * nz;
-    const int threads = 256;
-    const int64_t blocks = (n + threads - 1) / threads;
-    k_pals_eval<<<(unsigned)blocks, threads, 0, s>>>(p, m0, mu_in, mu_out, c, eps, gamma, nx, ny, nz, h, phi, mu, wdmu);
+    const int64_t tiles = (int64_t)((nx + kPalsTx - 1) / kPalsTx) * ((ny + kPalsTy - 1) / kPalsTy) *
+                          ((nz + kPalsTz - 1) / kPalsTz);
+    k_pals_eval<<<(unsigned)tiles, kPalsTx * kPalsTy * kPalsTz, 0, s>>>(p, m0, mu_in, mu_out, c, eps, gamma, nx, ny,
+                                                                       nz, h, phi, mu, wdmu);
     return cudaGetLastError();
 }
 

@@ -275,8 +275,8 @@ __global__ void __launch_bounds__(256) k_r(Op<T> op, const T* __restrict__ q, T*
         rr[u] = 0;
     }
     if (any) {
-        // two cells in flight per thread: the loop is bound by load latency, not issue
-#pragma unroll 2
+        // four cells in flight per thread: the loop is bound by load latency, not issue
+#pragma unroll 4
         VOXEL_LOOP(v) {
             const int64_t e = v * kp + c0;
             const V16<T> qv = ld16(q + e);
