@@ -84,14 +84,15 @@ typedef struct dot_stats {
 } dot_stats;
 
 /* Per-kernel device time of the Krylov kernels, accumulated while timing is on.
- * Index 0: stencil q = A p with p^T q; 1: x/r update with r^T M^{-1} r and ||r||^2;
- * 2: direction update p = M^{-1} r + beta p; 3: FP64 refinement residual b - A x.
+ * Index 0: stencil q = A p with p^T q; 1: r update with r^T M^{-1} r and ||r||^2;
+ * 2: direction update p = M^{-1} r + beta p; 3: FP64 refinement round (promotion,
+ * residual b - A x, rescaling); 4: x update from the ring of recent directions.
  * bytes: algorithmic DRAM bytes of those launches (each vector element of an
  * active column read or written once, coefficients once per launch). */
 typedef struct dot_kernel_timing {
-    int64_t launches[4];
-    double  ms[4];
-    double  bytes[4];
+    int64_t launches[5];
+    double  ms[5];
+    double  bytes[5];
 } dot_kernel_timing;
 
 /* Context: binds a CUDA device and owns every device buffer.

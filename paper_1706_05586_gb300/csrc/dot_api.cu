@@ -60,6 +60,22 @@ int ensure(DevBuf& b, size_t bytes) {
     return DOT_OK;
 }
 
+// ensure() without an error record: false (and b empty) when the allocation fails.
+bool try_ensure(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.p && b.bytes >= bytes) return true;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    b.bytes = bytes;
+    return true;
+}
+
 void release(DevBuf& b) {
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
@@ -81,6 +97,7 @@ struct SolveRun {
     size_t ei = 8;
     Launch L{}, Lv{};
     ColState st{};
+    DirRing ring;
     TmaStencil tma;
     bool tma_ready = false;
     OpRaw oi{}, o64{};
@@ -187,7 +204,8 @@ struct dot_ctx {
 
     // kernel timing (dot_set_kernel_timing)
     bool timing = false;
-    cudaEvent_t tev[8 * 4 + 2] = {};
+    // per-iteration events (4 x 8), refresh pair, one per flush of a batch (up to 4)
+    cudaEvent_t tev[8 * 4 + 2 + 4] = {};
     dot_kernel_timing kt{};
 };
 
@@ -275,7 +293,7 @@ int ensure_coefficients(dot_ctx* c) {
 
 int alloc_colstate(dot_ctx* c, int kp, int max_grid, ColState* st) {
     const size_t n16 = (size_t)kp * 16, n8 = (size_t)kp * 8, n4 = (size_t)kp * 4;
-    const size_t bytes = 4 * n16 + 7 * n8 + 6 * n4 + 64;
+    const size_t bytes = (4 + kDirRingMax) * n16 + 7 * n8 + 6 * n4 + 64;
     TRY(ensure(c->colbuf, bytes));
     const size_t groups = ((size_t)max_grid + kReduceGroup - 1) / kReduceGroup;
     TRY(ensure(c->partA, ((size_t)max_grid + groups) * kp * 16));
@@ -292,6 +310,7 @@ int alloc_colstate(dot_ctx* c, int kp, int max_grid, ColState* st) {
     st->rho = reinterpret_cast<double2*>(take(n16));
     st->rho_prev = reinterpret_cast<double2*>(take(n16));
     st->alpha = reinterpret_cast<double2*>(take(n16));
+    st->alpha_hist = reinterpret_cast<double2*>(take(kDirRingMax * n16));
     st->beta = reinterpret_cast<double2*>(take(n16));
     st->rr = reinterpret_cast<double*>(take(n8));
     st->maxr = reinterpret_cast<double*>(take(n8));
@@ -331,7 +350,7 @@ int read_counts(dot_ctx* c, const ColState& st, int* act, int* upd) {
 
 constexpr int kPoll = 8;  // iterations between host polls
 
-int collect_step_timing(dot_ctx* c, int steps, bool first_without_p) {
+int collect_step_timing(dot_ctx* c, int steps, bool first_without_p, int H) {
     for (int m = 0; m < steps; ++m) {
         float ms = 0.f;
         if (!(first_without_p && m == 0)) {
@@ -345,6 +364,11 @@ int collect_step_timing(dot_ctx* c, int steps, bool first_without_p) {
         CK(cudaEventElapsedTime(&ms, c->tev[4 * m + 2], c->tev[4 * m + 3]));
         c->kt.ms[1] += ms;
         c->kt.launches[1] += 1;
+        if (m % H == H - 1) {
+            CK(cudaEventElapsedTime(&ms, c->tev[4 * m + 3], c->tev[34 + m / H]));
+            c->kt.ms[4] += ms;
+            c->kt.launches[4] += 1;
+        }
     }
     return DOT_OK;
 }
@@ -364,7 +388,7 @@ int apply_tuning(dot_ctx* c, SolveRun& r, const Tuning& t) {
     const int64_t g = (int64_t)c->num_sms * t.blocks_per_sm;
     r.Lv.grid = (int)std::max<int64_t>(1, std::min(need, g));
     if (t.tma && !r.tma_ready) {
-        CK(tma_stencil_prepare(r.inner, c->pi.p, c->cf32.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma));
+        CK(tma_stencil_prepare(r.inner, r.ring, c->cf32.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma));
         r.tma_ready = true;
     }
     run_release_graph(r);
@@ -388,7 +412,19 @@ int solve_begin(dot_ctx* c, int kp, int kr) {
     const Launch Lmax = vector_launch(r.n, kp, vector_width(r.inner), c->num_sms);
     const int gmax = (int)std::min<int64_t>((r.n + Lmax.slots - 1) / Lmax.slots, (int64_t)c->num_sms * 16);
     TRY(alloc_colstate(c, kp, std::max(r.L.grid, std::max(gmax, 1)), &r.st));
-    for (DevBuf* b : {&c->xi, &c->ri, &c->pi, &c->qi}) TRY(ensure(*b, (size_t)r.n * kp * r.ei));
+    for (DevBuf* b : {&c->xi, &c->ri, &c->qi}) TRY(ensure(*b, (size_t)r.n * kp * r.ei));
+    // direction ring: as many slots (8, 4 or 2) as device memory allows
+    const size_t slot_bytes = (size_t)r.n * kp * r.ei;
+    r.ring = DirRing{};
+    for (int H = kDirRingMax; H >= 2; H /= 2) {
+        if (kPoll % H == 0 && try_ensure(c->pi, (size_t)H * slot_bytes)) {
+            r.ring = DirRing{c->pi.p, (int64_t)r.n * kp, H};
+            break;
+        }
+    }
+    if (!r.ring.base)
+        return fail(DOT_ENOMEM, "cudaMalloc of the direction ring (2 x " + std::to_string(slot_bytes) +
+                                    " bytes) failed");
     r.oi = r.mixed ? op32(c) : op64(c);
     r.o64 = op64(c);
     r.delta = r.mixed ? c->delta : 0.0;
@@ -410,7 +446,8 @@ int solve_begin(dot_ctx* c, int kp, int kr) {
         }
     }
     TRY(apply_tuning(c, r, base));
-    CK(solve_start(r.inner, r.oi, c->b64.p, c->x64.p, c->xi.p, c->ri.p, c->pi.p, r.n, kp, r.st, c->rtol, r.L, c->s));
+    CK(solve_start(r.inner, r.oi, c->b64.p, c->x64.p, c->xi.p, c->ri.p, r.ring.base, r.n, kp, r.st, c->rtol, r.L,
+                   c->s));
     count(c, 2);
     TRY(read_counts(c, r.st, &r.act, &r.upd));
     r.done = r.act == 0;
@@ -420,8 +457,9 @@ int solve_begin(dot_ctx* c, int kp, int kr) {
 int launch_batch(dot_ctx* c, SolveRun& r, bool first_batch) {
     for (int m = 0; m < kPoll; ++m) {
         const bool with_p = !(first_batch && m == 0);
-        CK(kry_step(r.inner, r.oi, c->xi.p, c->ri.p, c->pi.p, c->qi.p, r.n, r.kp, r.st, r.delta, r.maxit, with_p, r.Lv,
-                    r.cfg.tma ? &r.tma : nullptr, c->s, c->timing ? &c->tev[4 * m] : nullptr));
+        CK(kry_step(r.inner, r.oi, c->xi.p, c->ri.p, r.ring, m, c->qi.p, r.n, r.kp, r.st, r.delta, r.maxit, with_p,
+                    r.Lv, r.cfg.tma ? &r.tma : nullptr, c->s, c->timing ? &c->tev[4 * m] : nullptr,
+                    c->timing ? &c->tev[34 + m / r.ring.H] : nullptr));
     }
     return DOT_OK;
 }
@@ -462,7 +500,7 @@ int solve_advance(dot_ctx* c) {
     } else {
         TRY(launch_batch(c, r, first_batch));
     }
-    count(c, kPoll * 3 - (first_batch ? 1 : 0));
+    count(c, kPoll * 3 - (first_batch ? 1 : 0) + kPoll / r.ring.H);  // plus the ring flushes
     if (tuning) CK(cudaEventRecord(c->bev[1], c->s));
     r.first = false;
     r.it += kPoll;
@@ -475,7 +513,7 @@ int solve_poll(dot_ctx* c) {
     if (r.done) return DOT_OK;
     const bool first_batch = r.it == kPoll;
     TRY(read_counts(c, r.st, &r.act, &r.upd));
-    if (c->timing) TRY(collect_step_timing(c, kPoll, first_batch));
+    if (c->timing) TRY(collect_step_timing(c, kPoll, first_batch, r.ring.H));
     if (r.batch_timed) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->bev[0], c->bev[1]));
@@ -503,8 +541,8 @@ int solve_poll(dot_ctx* c) {
     }
     if (r.upd > 0) {
         if (c->timing) CK(cudaEventRecord(c->tev[32], c->s));
-        CK(solve_refresh(r.inner, r.oi, r.o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, c->ri.p, c->pi.p, r.n, r.kp,
-                         r.st, c->rtol, r.maxit, r.L, c->num_sms, c->s));
+        CK(solve_refresh(r.inner, r.oi, r.o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, c->ri.p, r.n, r.kp, r.st,
+                         c->rtol, r.maxit, r.L, c->num_sms, c->s));
         count(c, 3);
         if (c->timing) {
             CK(cudaEventRecord(c->tev[33], c->s));
@@ -513,7 +551,7 @@ int solve_poll(dot_ctx* c) {
             CK(cudaEventElapsedTime(&ms, c->tev[32], c->tev[33]));
             c->kt.ms[3] += ms;
             c->kt.launches[3] += 3;
-            c->kt.bytes[3] += (double)r.act * r.n * (6.0 * esz64(c) + 4.0 * r.ei) + (double)r.n * 4.0 * 8.0;
+            c->kt.bytes[3] += (double)r.act * r.n * (6.0 * esz64(c) + 3.0 * r.ei) + (double)r.n * 4.0 * 8.0;
         }
         TRY(read_counts(c, r.st, &r.act, &r.upd));
     }
@@ -532,7 +570,7 @@ int solve_end(dot_ctx* c) {
     CK(cudaStreamSynchronize(c->s));
     bool any_bad = r.act > 0;
     for (int j = 0; j < kp; ++j) any_bad = any_bad || status[j] != DOT_OK;
-    CK(solve_finish(r.inner, r.o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, c->pi.p, r.n, kp, r.st, any_bad, r.L, c->num_sms,
+    CK(solve_finish(r.inner, r.o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, r.n, kp, r.st, any_bad, r.L, c->num_sms,
                     c->s));
     count(c, any_bad ? 2 : 1);
     CK(cudaMemcpyAsync(iters.data(), r.st.iters, kp * 4, cudaMemcpyDeviceToHost, c->s));
@@ -549,7 +587,8 @@ int solve_end(dot_ctx* c) {
     if (c->timing) {
         // algorithmic bytes of the Krylov kernels: every element of a running column read or
         // written once per launch (stencil: p, q; update: r~, q read, r~ written; direction:
-        // r~, p, x~ read, p, x~ written), coefficients once per launch
+        // r~, old p read, new p written; flush: each direction once, x~ read and written
+        // once per ring), coefficients once per launch
         double ci = 0.0;
         int itmax = 0;
         for (int j = 0; j < kp; ++j) {
@@ -559,7 +598,8 @@ int solve_end(dot_ctx* c) {
         const double nn = (double)r.n, rs = r.mixed ? 4.0 : 8.0;
         c->kt.bytes[0] += ci * nn * 2.0 * r.ei + itmax * nn * 4.0 * rs;
         c->kt.bytes[1] += ci * nn * 3.0 * r.ei + itmax * nn * r.ei;
-        c->kt.bytes[2] += ci * nn * 5.0 * r.ei + itmax * nn * r.ei;
+        c->kt.bytes[2] += ci * nn * 3.0 * r.ei + itmax * nn * r.ei;
+        c->kt.bytes[4] += ci * nn * r.ei + ci / r.ring.H * nn * 2.0 * r.ei;
     }
     float ms_solve = 0;
     cudaEventElapsedTime(&ms_solve, c->ev[1], c->ev[2]);
@@ -745,7 +785,7 @@ int dot_create(dot_ctx** out, int device) {
     cudaError_t e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_flag, 8 * sizeof(int));
     for (int t = 0; t < 4 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->ev[t]);
-    for (int t = 0; t < 34 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->tev[t]);
+    for (int t = 0; t < 38 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->tev[t]);
     for (int t = 0; t < 2 && e == cudaSuccess; ++t) e = cudaEventCreate(&c->bev[t]);
     if (e != cudaSuccess) {
         dot_destroy(c);
@@ -767,7 +807,7 @@ int dot_destroy(dot_ctx* c) {
     for (DevBuf* b : bufs) release(*b);
     for (int t = 0; t < 4; ++t)
         if (c->ev[t]) cudaEventDestroy(c->ev[t]);
-    for (int t = 0; t < 34; ++t)
+    for (int t = 0; t < 38; ++t)
         if (c->tev[t]) cudaEventDestroy(c->tev[t]);
     for (int t = 0; t < 2; ++t)
         if (c->bev[t]) cudaEventDestroy(c->bev[t]);

@@ -15,10 +15,15 @@ int record_error(int code, const std::string& msg);
 
 // Per-column Krylov state of one block solve (device pointers, length kp unless noted).
 // The recurrence runs on r~ = r / scale; the FP64 solution and true residual are separate.
+// Slots of the direction ring: the search directions of up to this many consecutive
+// iterations are kept, and x~ takes their corrections in one pass per ring.
+constexpr int kDirRingMax = 8;
+
 struct ColState {
     double2* rho;      // r~^T M^{-1} r~ (bilinear; imaginary part 0 in real arithmetic)
     double2* rho_prev; // rho of the previous iteration (the denominator of beta)
     double2* alpha;
+    double2* alpha_hist; // [kDirRingMax][kp] alpha of each iteration of the current direction ring (0: not run)
     double2* beta;
     double* rr;        // ||r~||^2 of the recurrence
     double* maxr;      // max ||r~|| since the last reliable update
@@ -64,8 +69,16 @@ struct Launch {
 };
 
 // TMA-staged stencil (stencil_tma.cu): tensor map over the p block and launch shape.
+// The search directions of the last H iterations: slot (iteration mod H) receives
+// the new direction, slot (iteration - 1) mod H holds the previous one.
+struct DirRing {
+    void* base = nullptr;    // H consecutive slots of n x kp recurrence-type elements
+    int64_t slot_elems = 0;  // elements per slot
+    int H = 0;               // slots in use: 8, 4 or 2 (a divisor of the poll batch)
+};
+
 struct TmaStencil {
-    alignas(64) unsigned char tmap[128];     // CUtensorMap of p
+    alignas(64) unsigned char tmap[kDirRingMax][128];  // CUtensorMap of each ring slot
     alignas(64) unsigned char tmap_cf[128];  // CUtensorMap of the packed coefficients
     int kc = 32;                          // columns per tile (32, or 16)
     int zc = 0;                           // z planes per work item
@@ -73,9 +86,11 @@ struct TmaStencil {
     size_t smem = 0;
 };
 bool tma_stencil_eligible(ElemKind inner, int nx, int ny, int kp);
-cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, const void* cf, int nx, int ny, int nz, int kp,
+cudaError_t tma_stencil_prepare(ElemKind inner, const DirRing& ring, const void* cf, int nx, int ny, int nz, int kp,
                                 int num_sms, TmaStencil* out);
-cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& op, const TmaStencil& t, void* q, int kp,
+// q = A p for the direction in ring slot `slot` (its alpha goes to row `slot` of the
+// step-length history).
+cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& op, const TmaStencil& t, int slot, void* q, int kp,
                                const ColState& st, cudaStream_t s);
 
 // Launch shape of the scalar kernels (one column per thread, four blocks per SM).
@@ -90,21 +105,21 @@ int vector_width(ElemKind inner);
 // in complexity.
 cudaError_t solve_start(ElemKind inner, const OpRaw& op, const void* b64, void* x64, void* x, void* r, void* p,
                         int64_t n, int kp, const ColState& st, double rtol, const Launch& L, cudaStream_t s);
-// One Krylov iteration: [direction update,] stencil q = A p with p^T q, then
-// x~/r~ update with convergence / refresh decisions.  ev, when not null, receives
-// four event records around the three launches.
-cudaError_t kry_step(ElemKind inner, const OpRaw& op, void* x, void* r, void* p, void* q, int64_t n, int kp,
-                     const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv,
-                     const TmaStencil* tma, cudaStream_t s, cudaEvent_t* ev);
-// Reliable update of the active columns: promote x~ (with the correction alpha p still
-// pending from the last iteration), FP64 true residual, rescale r~.
+// Krylov iteration m of a batch (the batch starts at a multiple of the ring size):
+// [direction update into slot m mod H,] stencil q = A p with p^T q, r~ update with
+// convergence / refresh decisions, and, when slot m mod H is the ring's last, the
+// flush x~ += sum_j alpha_j p_j.  ev, when not null, receives four event records
+// around the first three launches; evf, when not null, one record after the flush.
+cudaError_t kry_step(ElemKind inner, const OpRaw& op, void* x, void* r, const DirRing& ring, int m, void* q,
+                     int64_t n, int kp, const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv,
+                     const TmaStencil* tma, cudaStream_t s, cudaEvent_t* ev, cudaEvent_t* evf);
+// Reliable update of the active columns (after a flush): promote x~, FP64 true
+// residual, rescale r~.
 cudaError_t solve_refresh(ElemKind inner, const OpRaw& op, const OpRaw& op64, const void* b64, void* x64, void* r64,
-                          void* x, void* r, const void* p, int64_t n, int kp, const ColState& st, double rtol, int maxit,
+                          void* x, void* r, int64_t n, int kp, const ColState& st, double rtol, int maxit,
                           const Launch& L, int num_sms, cudaStream_t s);
-// Promote every column's x~ (and pending alpha p); optionally recompute every column's
-// true residual.
-cudaError_t solve_finish(ElemKind inner, const OpRaw& op64, const void* b64, void* x64, void* r64, void* x,
-                         const void* p, int64_t n,
+// Promote every column's x~; optionally recompute every column's true residual.
+cudaError_t solve_finish(ElemKind inner, const OpRaw& op64, const void* b64, void* x64, void* r64, void* x, int64_t n,
                          int kp, const ColState& st, bool residual, const Launch& L, int num_sms, cudaStream_t s);
 cudaError_t op_apply(ElemKind ek, const OpRaw& op, const void* x, void* y, int64_t n, int kp,
                      cudaStream_t s);

@@ -137,6 +137,26 @@ static __device__ __noinline__ bool reduce_columns(const ColState& st, bool useA
     return true;
 }
 
+// Finaliser of the stencil kernels: alpha = rho / p^T q on the running columns
+// (breakdown on a zero or non-finite p^T q), and row hslot of the step-length
+// history records alpha, 0 for every column that did not take this iteration.
+static __device__ __noinline__ void stencil_finalise(const ColState& st, const double2* totA, int kp, int hslot) {
+    for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
+        double2 al = make_double2(0.0, 0.0);
+        if (st.active[cc] && !st.upd[cc]) {
+            const double2 a = totA[cc];
+            if (!zfinite(a) || (a.x == 0.0 && a.y == 0.0)) {
+                st.status[cc] = DOT_EBREAKDOWN;
+                st.active[cc] = 0;
+            } else {
+                al = zdiv(st.rho[cc], a);
+            }
+        }
+        st.alpha[cc] = al;
+        st.alpha_hist[(int64_t)hslot * kp + cc] = al;
+    }
+}
+
 // Column counters written by the finalisers: active columns and columns paused for
 // a reliable update.  Also re-arms the second-level arrival counter.
 static __device__ __forceinline__ void publish_counts(const ColState& st, int kp) {

@@ -73,7 +73,7 @@ __global__ void k_start_norm(const T64* __restrict__ b, T64* __restrict__ x64, i
             st.upd[cc] = 0;
             st.updates[cc] = 0;
             st.since[cc] = 0;
-            st.alpha[cc] = make_double2(0.0, 0.0);  // no correction alpha p pending
+            st.alpha[cc] = make_double2(0.0, 0.0);
             st.status[cc] = fin ? DOT_OK : DOT_EBREAKDOWN;
             st.active[cc] = fin && bsum > 0.0;
         }
@@ -175,7 +175,7 @@ __device__ __forceinline__ void column_partials_w(const double2 (&a)[W], const d
 // neighbour moves W columns; the grid keeps eight blocks per SM in flight.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T* __restrict__ q, int kp,
-                                               int slots, ColState st) {
+                                               int slots, ColState st, int hslot) {
     using R = typename Elem<T>::R;
     constexpr int W = Vec16<T>::W;
     const int tpv = kp / W;
@@ -232,27 +232,16 @@ __global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T
     const double2* totA;
     const double* totB;
     if (reduce_columns(st, true, false, kp, smem_raw, &totA, &totB)) {
-        for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-            if (!running(st, cc)) continue;
-            const double2 a = totA[cc];
-            const double unused = totB[cc];
-            if (!zfinite(a) || (a.x == 0.0 && a.y == 0.0)) {
-                st.status[cc] = DOT_EBREAKDOWN;
-                st.active[cc] = 0;
-                st.alpha[cc] = make_double2(0.0, 0.0);  // the last correction is in x~ already
-                continue;
-            }
-            st.alpha[cc] = zdiv(st.rho[cc], a);
-        }
+        stencil_finalise(st, totA, kp, hslot);
         __syncthreads();
         publish_counts(st, kp);
     }
 }
 
 // r~ -= alpha q, rho' = r~^T M^{-1} r~, ||r~||^2 on the running columns (the others
-// are left untouched).  The matching x~ += alpha p is deferred to the next direction
-// update, which reads p anyway (or to the refresh, if the column pauses), so this
-// pass streams two vectors instead of four.  Finaliser: pause the column for a
+// are left untouched).  The matching x~ += alpha p waits for the flush that closes
+// the direction ring (k_flush), so this pass streams two vectors instead of four.
+// Finaliser: pause the column for a
 // reliable update when ||r~|| reached the target, fell below delta * max||r~|| or
 // went kRefreshEvery iterations without a refresh; otherwise beta = rho' / rho.
 template <typename T>
@@ -342,74 +331,104 @@ __global__ void __launch_bounds__(256) k_r(Op<T> op, const T* __restrict__ q, T*
     }
 }
 
-// x~ += alpha p (the correction of the previous iteration, where one is pending),
-// then p = M^{-1} r~ + beta p, on the running columns.
+// p_new = M^{-1} r~ + beta p_old on the running columns, where p_old and p_new are
+// consecutive slots of the direction ring.  Paused columns carry p_old over, so that
+// they resume from the slot the next iteration reads; stopped columns are skipped.
 template <typename T>
-__global__ void __launch_bounds__(256) k_px(Op<T> op, const T* __restrict__ r, T* __restrict__ p, T* __restrict__ x,
-                                            int64_t n, int kp, int slots, ColState st) {
+__global__ void __launch_bounds__(256) k_dir(Op<T> op, const T* __restrict__ r, const T* __restrict__ p_old,
+                                             T* __restrict__ p_new, int64_t n, int kp, int slots, ColState st) {
     constexpr int W = Vec16<T>::W;
     const int tpv = kp / W;
     const int t = threadIdx.x % tpv, slot = threadIdx.x / tpv, c0 = t * W;
-    bool run[W], corr[W];
-    bool any = false, anyx = false;
-    T beta[W], alpha[W];
+    bool run[W];
+    bool anyrun = false, anyact = false;
+    T beta[W];
 #pragma unroll
     for (int u = 0; u < W; ++u) {
         run[u] = running(st, c0 + u);
-        any = any || run[u];
+        anyrun = anyrun || run[u];
+        anyact = anyact || st.active[c0 + u] != 0;
         beta[u] = run[u] ? enarrow<T>(st.beta[c0 + u]) : ezero<T>();
-        const double2 a = st.alpha[c0 + u];
-        corr[u] = run[u] && (a.x != 0.0 || a.y != 0.0);
-        anyx = anyx || corr[u];
-        alpha[u] = corr[u] ? enarrow<T>(a) : ezero<T>();
     }
-    if (!any) return;
-    if (anyx) {
+    if (anyrun) {
         VOXEL_LOOP(v) {
             const int64_t e = v * kp + c0;
             const V16<T> rv = ld16(r + e);
-            V16<T> pv = ld16(p + e), xv = ld16(x + e);
-            const T dv = op.dinv[v];
-#pragma unroll
-            for (int u = 0; u < W; ++u) {
-                if (corr[u]) xv.e[u] = eadd(xv.e[u], emul(alpha[u], pv.e[u]));
-                if (run[u]) pv.e[u] = eadd(emul(dv, rv.e[u]), emul(beta[u], pv.e[u]));
-            }
-            st16(x + e, xv);
-            st16(p + e, pv);
-        }
-    } else {
-        VOXEL_LOOP(v) {
-            const int64_t e = v * kp + c0;
-            const V16<T> rv = ld16(r + e);
-            V16<T> pv = ld16(p + e);
+            V16<T> pv = ld16(p_old + e);
             const T dv = op.dinv[v];
 #pragma unroll
             for (int u = 0; u < W; ++u)
                 if (run[u]) pv.e[u] = eadd(emul(dv, rv.e[u]), emul(beta[u], pv.e[u]));
-            st16(p + e, pv);
+            st16(p_new + e, pv);
+        }
+    } else if (anyact) {
+        VOXEL_LOOP(v) {
+            const int64_t e = v * kp + c0;
+            st16(p_new + e, ld16(p_old + e));
         }
     }
 }
 
+// x~ += sum_j alpha_j p_j over the H slots of the direction ring, in iteration order
+// (the same sequence of roundings as adding each correction when it is made).  A
+// slot whose alpha is 0 (the column did not run in that iteration) adds nothing: its
+// value is selected away after the load, never multiplied, so a slot that was never
+// written for a column cannot reach x~.  When every slot holds a correction for one
+// of the thread's columns (the common case) all H loads are issued back to back.
+template <typename T, int H>
+__global__ void __launch_bounds__(256) k_flush(const T* __restrict__ ring, int64_t slot_elems,
+                                               T* __restrict__ x, int64_t n, int kp, int slots, ColState st) {
+    constexpr int W = Vec16<T>::W;
+    const int tpv = kp / W;
+    const int t = threadIdx.x % tpv, slot = threadIdx.x / tpv, c0 = t * W;
+    T al[H][W];
+    bool on[H][W];
+    unsigned use = 0;  // bit j: some column of this thread has a correction in slot j
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const double2 a = st.alpha_hist[(int64_t)j * kp + c0 + u];
+            on[j][u] = a.x != 0.0 || a.y != 0.0;
+            al[j][u] = enarrow<T>(a);
+            if (on[j][u]) use |= 1u << j;
+        }
+    }
+    if (!use) return;
+    VOXEL_LOOP(v) {
+        const int64_t e = v * kp + c0;
+        V16<T> xv = ld16(x + e);
+        V16<T> pv[H];
+        if (use == (1u << H) - 1u) {
+#pragma unroll
+            for (int j = 0; j < H; ++j) pv[j] = ld16(ring + j * slot_elems + e);
+        } else {
+#pragma unroll
+            for (int j = 0; j < H; ++j)
+                if (use & (1u << j)) pv[j] = ld16(ring + j * slot_elems + e);
+        }
+#pragma unroll
+        for (int j = 0; j < H; ++j)
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+                if (on[j][u]) xv.e[u] = eadd(xv.e[u], emul(al[j][u], pv[j].e[u]));
+        st16(x + e, xv);
+    }
+}
+
 // ------------------------------------------------------------ reliable update
-// x64 += s (x~ + alpha p), x~ = 0 on the active columns (every column when all !=
-// 0), where alpha p is the correction still pending from the column's last
-// iteration (alpha = 0 when there is none).
+// x64 += s x~, x~ = 0 on the active columns (every column when all != 0).  Runs
+// between batches, after the flush of the direction ring, so x~ holds every
+// correction made so far.
 template <typename T64, typename T>
-__global__ void k_promote(T64* __restrict__ x64, T* __restrict__ x, const T* __restrict__ p, int64_t n, int kp,
-                          int slots, ColState st, int all) {
+__global__ void k_promote(T64* __restrict__ x64, T* __restrict__ x, int64_t n, int kp, int slots, ColState st,
+                          int all) {
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
     if (!(all || st.active[c])) return;
     const double s = st.scale[c];
-    const double2 a = st.alpha[c];
-    const bool corr = a.x != 0.0 || a.y != 0.0;
-    const T alpha = enarrow<T>(a);
     VOXEL_LOOP(v) {
         const int64_t e = v * kp + c;
-        T xv = x[e];
-        if (corr) xv = eadd(xv, emul(alpha, p[e]));
-        const double2 d = ewide(xv);
+        const double2 d = ewide(x[e]);
         x64[e] = eadd(x64[e], enarrow<T64>(make_double2(s * d.x, s * d.y)));
         x[e] = ezero<T>();
     }
@@ -483,7 +502,6 @@ __global__ void k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64
             const double rsum = totB[cc];
             st.rr64[cc] = rsum;
             if (all) continue;
-            st.alpha[cc] = make_double2(0.0, 0.0);  // the pending correction was promoted
             st.updates[cc] += 1;
             if (!isfinite(rsum)) {
                 st.status[cc] = DOT_EBREAKDOWN;
@@ -620,24 +638,40 @@ static void record_timing(cudaEvent_t ev, cudaStream_t s) {
         cudaEventRecord(ev, s);
 }
 
-cudaError_t kry_step(ElemKind inner, const OpRaw& o, void* x, void* r, void* p, void* q, int64_t n, int kp,
-                     const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv,
-                     const TmaStencil* tma, cudaStream_t s, cudaEvent_t* ev) {
+cudaError_t kry_step(ElemKind inner, const OpRaw& o, void* x, void* r, const DirRing& ring, int m, void* q,
+                     int64_t n, int kp, const ColState& st, double delta, int maxit, bool with_p, const Launch& Lv,
+                     const TmaStencil* tma, cudaStream_t s, cudaEvent_t* ev, cudaEvent_t* evf) {
+    const int H = ring.H;
+    const int slot = m % H, prev = (slot + H - 1) % H;
     DOT_DISPATCH2(inner, {
         Op<T> op = make_op<T>(o);
         const size_t sm = red_smem(Lv, kp);
+        T* base = static_cast<T*>(ring.base);
+        T* p_new = base + slot * ring.slot_elems;
+        const T* p_old = base + prev * ring.slot_elems;
         if (ev) record_timing(ev[0], s);
-        if (with_p) k_px<T><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, (T*)p, (T*)x, n, kp, Lv.slots, st);
+        if (with_p)
+            k_dir<T><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, p_old, p_new, n, kp, Lv.slots, st);
         if (ev) record_timing(ev[1], s);
         if (tma) {
-            const cudaError_t e = tma_stencil_launch(inner, o, *tma, q, kp, st, s);
+            const cudaError_t e = tma_stencil_launch(inner, o, *tma, slot, q, kp, st, s);
             if (e != cudaSuccess) return e;
         } else {
-            k_pq<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)p, (T*)q, kp, Lv.slots, st);
+            k_pq<T><<<Lv.grid, Lv.threads, sm, s>>>(op, p_new, (T*)q, kp, Lv.slots, st, slot);
         }
         if (ev) record_timing(ev[2], s);
         k_r<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)q, (T*)r, n, kp, Lv.slots, st, delta, maxit);
         if (ev) record_timing(ev[3], s);
+        if (slot == H - 1) {
+            const T* rb = base;
+            if (H == 8)
+                k_flush<T, 8><<<Lv.grid, Lv.threads, 0, s>>>(rb, ring.slot_elems, (T*)x, n, kp, Lv.slots, st);
+            else if (H == 4)
+                k_flush<T, 4><<<Lv.grid, Lv.threads, 0, s>>>(rb, ring.slot_elems, (T*)x, n, kp, Lv.slots, st);
+            else
+                k_flush<T, 2><<<Lv.grid, Lv.threads, 0, s>>>(rb, ring.slot_elems, (T*)x, n, kp, Lv.slots, st);
+            if (evf) record_timing(*evf, s);
+        }
         (void)sizeof(T64);
     });
     return cudaGetLastError();
@@ -653,11 +687,11 @@ int vector_width(ElemKind inner) {
 }
 
 cudaError_t solve_refresh(ElemKind inner, const OpRaw& o, const OpRaw& o64, const void* b64, void* x64, void* r64,
-                          void* x, void* r, const void* p, int64_t n, int kp, const ColState& st, double rtol, int maxit,
+                          void* x, void* r, int64_t n, int kp, const ColState& st, double rtol, int maxit,
                           const Launch& L, int num_sms, cudaStream_t s) {
     (void)num_sms;
     DOT_DISPATCH2(inner, {
-        k_promote<T64, T><<<L.grid, L.threads, 0, s>>>((T64*)x64, (T*)x, (const T*)p, n, kp, L.slots, st, 0);
+        k_promote<T64, T><<<L.grid, L.threads, 0, s>>>((T64*)x64, (T*)x, n, kp, L.slots, st, 0);
         k_true_residual<T64><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<T64>(o64), (const T64*)b64,
                                                                         (const T64*)x64, (T64*)r64, n, kp, L.slots,
                                                                         st, rtol, maxit, 0);
@@ -667,12 +701,11 @@ cudaError_t solve_refresh(ElemKind inner, const OpRaw& o, const OpRaw& o64, cons
     return cudaGetLastError();
 }
 
-cudaError_t solve_finish(ElemKind inner, const OpRaw& o64, const void* b64, void* x64, void* r64, void* x,
-                         const void* p, int64_t n,
+cudaError_t solve_finish(ElemKind inner, const OpRaw& o64, const void* b64, void* x64, void* r64, void* x, int64_t n,
                          int kp, const ColState& st, bool residual, const Launch& L, int num_sms, cudaStream_t s) {
     (void)num_sms;
     DOT_DISPATCH2(inner, {
-        k_promote<T64, T><<<L.grid, L.threads, 0, s>>>((T64*)x64, (T*)x, (const T*)p, n, kp, L.slots, st, 1);
+        k_promote<T64, T><<<L.grid, L.threads, 0, s>>>((T64*)x64, (T*)x, n, kp, L.slots, st, 1);
         if (residual)
             k_true_residual<T64><<<L.grid, L.threads, red_smem(L, kp), s>>>(make_op<T64>(o64), (const T64*)b64,
                                                                             (const T64*)x64, (T64*)r64, n, kp,

@@ -98,7 +98,8 @@ __device__ __forceinline__ void tma_plane(const CUtensorMap* tm, const CUtensorM
 template <typename T, int KC>
 __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __grid_constant__ CUtensorMap tm,
                                                        const __grid_constant__ CUtensorMap tc, Op<T> op,
-                                                       T* __restrict__ q, int kp, int zc_len, ColState st) {
+                                                       T* __restrict__ q, int kp, int zc_len, ColState st,
+                                                       int hslot) {
     using R = typename Elem<T>::R;
     constexpr int PLANE = KC * HX * HY;  // elements
     constexpr int P_BYTES = PLANE * sizeof(T);
@@ -243,16 +244,7 @@ __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __gr
     const double2* totA;
     const double* totB;
     if (reduce_columns(st, true, false, kp, base, &totA, &totB)) {
-        for (int cc = threadIdx.x; cc < kp; cc += blockDim.x) {
-            if (!(st.active[cc] && !st.upd[cc])) continue;
-            const double2 a = totA[cc];
-            if (!zfinite(a) || (a.x == 0.0 && a.y == 0.0)) {
-                st.status[cc] = DOT_EBREAKDOWN;
-                st.active[cc] = 0;
-                continue;
-            }
-            st.alpha[cc] = zdiv(st.rho[cc], a);
-        }
+        stencil_finalise(st, totA, kp, hslot);
         __syncthreads();
         publish_counts(st, kp);
     }
@@ -290,7 +282,7 @@ static cudaError_t tma_configure(size_t smem, int* per_sm) {
     return e;
 }
 
-cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, const void* cf, int nx, int ny, int nz, int kp,
+cudaError_t tma_stencil_prepare(ElemKind inner, const DirRing& ring, const void* cf, int nx, int ny, int nz, int kp,
                                 int num_sms, TmaStencil* out) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
@@ -300,12 +292,15 @@ cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, const void* cf, i
     const cuuint64_t strides[3] = {(cuuint64_t)kp * es, (cuuint64_t)kp * nx * es, (cuuint64_t)kp * nx * ny * es};
     const cuuint32_t box[4] = {(cuuint32_t)kc, HX, HY, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = enc(reinterpret_cast<CUtensorMap*>(out->tmap), inner == EK_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64
-                                                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                           4, const_cast<void*>(p), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    if (ring.H < 1 || ring.H > kDirRingMax) return cudaErrorInvalidValue;
+    for (int sl = 0; sl < ring.H; ++sl) {
+        void* p = static_cast<unsigned char*>(ring.base) + (size_t)sl * ring.slot_elems * es;
+        const CUresult r = enc(reinterpret_cast<CUtensorMap*>(out->tmap[sl]),
+                               inner == EK_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                               p, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
     // packed coefficients {cx, cy, cz, dre} per cell, FP32 for both recurrence types
     const cuuint64_t cdims[4] = {4, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     const cuuint64_t cstrides[3] = {16, (cuuint64_t)nx * 16, (cuuint64_t)nx * ny * 16};
@@ -347,9 +342,10 @@ cudaError_t tma_stencil_prepare(ElemKind inner, const void* p, const void* cf, i
     return cudaSuccess;
 }
 
-cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil& t, void* q, int kp,
+cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil& t, int slot, void* q, int kp,
                                const ColState& st, cudaStream_t s) {
-    const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(t.tmap);
+    if (slot < 0 || slot >= kDirRingMax) return cudaErrorInvalidValue;
+    const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(t.tmap[slot]);
     const CUtensorMap* tc = reinterpret_cast<const CUtensorMap*>(t.tmap_cf);
     if (inner == EK_C64) {
         Op<float2> op;
@@ -360,9 +356,9 @@ cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil&
         op.ny = o.ny;
         op.nz = o.nz;
         if (t.kc == 32)
-            k_pq_tma<float2, 32><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float2*)q, kp, t.zc, st);
+            k_pq_tma<float2, 32><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float2*)q, kp, t.zc, st, slot);
         else
-            k_pq_tma<float2, 16><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float2*)q, kp, t.zc, st);
+            k_pq_tma<float2, 16><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float2*)q, kp, t.zc, st, slot);
     } else if (inner == EK_F32) {
         Op<float> op;
         op.cf = static_cast<const Cf4<float>*>(o.cf);
@@ -372,9 +368,9 @@ cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil&
         op.ny = o.ny;
         op.nz = o.nz;
         if (t.kc == 32)
-            k_pq_tma<float, 32><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st);
+            k_pq_tma<float, 32><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st, slot);
         else
-            k_pq_tma<float, 16><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st);
+            k_pq_tma<float, 16><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st, slot);
     } else {
         return cudaErrorInvalidValue;
     }

@@ -84,10 +84,10 @@ class DotStats(C.Structure):
 
 
 class DotKernelTiming(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4), ("bytes", C.c_double * 4)]
+    _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5), ("bytes", C.c_double * 5)]
 
     def as_dict(self):
-        names = ("stencil", "update", "direction", "refine_residual")
+        names = ("stencil", "update", "direction", "refine_residual", "flush")
         return {nm: {"launches": int(self.launches[i]), "ms": float(self.ms[i]), "bytes": float(self.bytes[i])}
                 for i, nm in enumerate(names)}
 
