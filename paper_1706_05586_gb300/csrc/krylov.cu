@@ -351,6 +351,7 @@ __global__ void __launch_bounds__(256) k_dir(Op<T> op, const T* __restrict__ r, 
         beta[u] = run[u] ? enarrow<T>(st.beta[c0 + u]) : ezero<T>();
     }
     if (anyrun) {
+#pragma unroll 2
         VOXEL_LOOP(v) {
             const int64_t e = v * kp + c0;
             const V16<T> rv = ld16(r + e);
