@@ -49,6 +49,12 @@ CASES = {
                                              ls=24, ld=24, m0=5, sampling="gaussian", seed_index=67),
     "real_24x8x7_k16": synth.small_workload(24, 8, 7, 0.3, src_grid=(3, 3), det_grid=(3, 3), ls=8, ld=8,
                                             m0=4, sampling="gaussian", seed_index=68),
+    # degenerate depth: a single layer of cells (no z neighbours), TMA path
+    "real_16x16x1_k32": synth.small_workload(16, 16, 1, 0.3, src_grid=(4, 4), det_grid=(4, 4), ls=16, ld=16,
+                                             m0=4, sampling="gaussian", seed_index=69),
+    # a wide block: 128 + 128 columns (eight 32-column tiles, 256 column accumulators per block)
+    "cplx_8x8x6_k256": synth.small_workload(8, 8, 6, 0.3, omega_nu=0.4, src_grid=(4, 4), det_grid=(4, 4), ls=128,
+                                            ld=128, m0=3, sampling="gaussian", seed_index=70),
     # the 100 MHz frequency on a 24x20x12 grid
     "cplx_24x20x12_100MHz": synth.small_workload(24, 20, 12, 0.25, omega_nu=synth.OMEGA_NU_100MHZ, src_grid=(3, 3),
                                                  det_grid=(3, 3), ls=4, ld=4, m0=8, sampling="gaussian",
@@ -250,7 +256,8 @@ def test_forward_model_all_sources(name, ctx):
     assert misfit_err(f, out) <= 1e-10
 
 
-@pytest.mark.parametrize("name", ["cplx_24x16x10_k32", "real_16x16x9_k32", "cplx_16x24x8_k48", "real_24x8x7_k16"])
+@pytest.mark.parametrize("name", ["cplx_24x16x10_k32", "real_16x16x9_k32", "cplx_16x24x8_k48", "real_24x8x7_k16",
+                                  "real_16x16x1_k32", "cplx_8x8x6_k256"])
 def test_tma_stencil_matches_direct_load_kernel(name, ctx):
     """The TMA-staged stencil and the direct-load stencil give the same solve to rounding."""
     pb, ref = _case(name)
