@@ -173,8 +173,8 @@ __device__ __forceinline__ void column_partials_w(const double2 (&a)[W], const d
 
 // q = A p and pq = p^T q; finaliser alpha = rho / pq.  One 16-byte load per
 // neighbour moves W columns; the grid keeps eight blocks per SM in flight.
-template <typename T>
-__global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T* __restrict__ q, int kp,
+template <typename T, int MT>
+__global__ void __launch_bounds__(MT) k_pq(Op<T> op, const T* __restrict__ p, T* __restrict__ q, int kp,
                                                int slots, ColState st, int hslot) {
     using R = typename Elem<T>::R;
     constexpr int W = Vec16<T>::W;
@@ -244,8 +244,8 @@ __global__ void __launch_bounds__(256) k_pq(Op<T> op, const T* __restrict__ p, T
 // Finaliser: pause the column for a
 // reliable update when ||r~|| reached the target, fell below delta * max||r~|| or
 // went kRefreshEvery iterations without a refresh; otherwise beta = rho' / rho.
-template <typename T>
-__global__ void __launch_bounds__(256) k_r(Op<T> op, const T* __restrict__ q, T* __restrict__ r, int64_t n, int kp,
+template <typename T, int MT>
+__global__ void __launch_bounds__(MT) k_r(Op<T> op, const T* __restrict__ q, T* __restrict__ r, int64_t n, int kp,
                                            int slots, ColState st, double delta, int maxit) {
     using R = typename Elem<T>::R;
     constexpr int W = Vec16<T>::W;
@@ -334,8 +334,8 @@ __global__ void __launch_bounds__(256) k_r(Op<T> op, const T* __restrict__ q, T*
 // p_new = M^{-1} r~ + beta p_old on the running columns, where p_old and p_new are
 // consecutive slots of the direction ring.  Paused columns carry p_old over, so that
 // they resume from the slot the next iteration reads; stopped columns are skipped.
-template <typename T>
-__global__ void __launch_bounds__(256) k_dir(Op<T> op, const T* __restrict__ r, const T* __restrict__ p_old,
+template <typename T, int MT>
+__global__ void __launch_bounds__(MT) k_dir(Op<T> op, const T* __restrict__ r, const T* __restrict__ p_old,
                                              T* __restrict__ p_new, int64_t n, int kp, int slots, ColState st) {
     constexpr int W = Vec16<T>::W;
     const int tpv = kp / W;
@@ -376,8 +376,8 @@ __global__ void __launch_bounds__(256) k_dir(Op<T> op, const T* __restrict__ r, 
 // value is selected away after the load, never multiplied, so a slot that was never
 // written for a column cannot reach x~.  When every slot holds a correction for one
 // of the thread's columns (the common case) all H loads are issued back to back.
-template <typename T, int H>
-__global__ void __launch_bounds__(256) k_flush(const T* __restrict__ ring, int64_t slot_elems,
+template <typename T, int H, int MT>
+__global__ void __launch_bounds__(MT) k_flush(const T* __restrict__ ring, int64_t slot_elems,
                                                T* __restrict__ x, int64_t n, int kp, int slots, ColState st) {
     constexpr int W = Vec16<T>::W;
     const int tpv = kp / W;
@@ -650,27 +650,49 @@ cudaError_t kry_step(ElemKind inner, const OpRaw& o, void* x, void* r, const Dir
         T* base = static_cast<T*>(ring.base);
         T* p_new = base + slot * ring.slot_elems;
         const T* p_old = base + prev * ring.slot_elems;
+        // blocks wider than 256 threads (one column per thread at block widths above
+        // 256 x the vector width) take the instantiations compiled for 1024 threads
+        const bool wide = Lv.threads > 256;
         if (ev) record_timing(ev[0], s);
-        if (with_p)
-            k_dir<T><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, p_old, p_new, n, kp, Lv.slots, st);
+        if (with_p) {
+            if (wide)
+                k_dir<T, 1024><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, p_old, p_new, n, kp, Lv.slots, st);
+            else
+                k_dir<T, 256><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, p_old, p_new, n, kp, Lv.slots, st);
+        }
         if (ev) record_timing(ev[1], s);
         if (tma) {
             const cudaError_t e = tma_stencil_launch(inner, o, *tma, slot, q, kp, st, s);
             if (e != cudaSuccess) return e;
+        } else if (wide) {
+            k_pq<T, 1024><<<Lv.grid, Lv.threads, sm, s>>>(op, p_new, (T*)q, kp, Lv.slots, st, slot);
         } else {
-            k_pq<T><<<Lv.grid, Lv.threads, sm, s>>>(op, p_new, (T*)q, kp, Lv.slots, st, slot);
+            k_pq<T, 256><<<Lv.grid, Lv.threads, sm, s>>>(op, p_new, (T*)q, kp, Lv.slots, st, slot);
         }
         if (ev) record_timing(ev[2], s);
-        k_r<T><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)q, (T*)r, n, kp, Lv.slots, st, delta, maxit);
+        if (wide)
+            k_r<T, 1024><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)q, (T*)r, n, kp, Lv.slots, st, delta, maxit);
+        else
+            k_r<T, 256><<<Lv.grid, Lv.threads, sm, s>>>(op, (const T*)q, (T*)r, n, kp, Lv.slots, st, delta, maxit);
         if (ev) record_timing(ev[3], s);
         if (slot == H - 1) {
             const T* rb = base;
-            if (H == 8)
-                k_flush<T, 8><<<Lv.grid, Lv.threads, 0, s>>>(rb, ring.slot_elems, (T*)x, n, kp, Lv.slots, st);
-            else if (H == 4)
-                k_flush<T, 4><<<Lv.grid, Lv.threads, 0, s>>>(rb, ring.slot_elems, (T*)x, n, kp, Lv.slots, st);
-            else
-                k_flush<T, 2><<<Lv.grid, Lv.threads, 0, s>>>(rb, ring.slot_elems, (T*)x, n, kp, Lv.slots, st);
+            const int64_t se = ring.slot_elems;
+            if (wide) {
+                if (H == 8)
+                    k_flush<T, 8, 1024><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+                else if (H == 4)
+                    k_flush<T, 4, 1024><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+                else
+                    k_flush<T, 2, 1024><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+            } else {
+                if (H == 8)
+                    k_flush<T, 8, 256><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+                else if (H == 4)
+                    k_flush<T, 4, 256><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+                else
+                    k_flush<T, 2, 256><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+            }
             if (evf) record_timing(*evf, s);
         }
         (void)sizeof(T64);

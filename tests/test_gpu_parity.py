@@ -273,3 +273,30 @@ def test_tma_stencil_matches_direct_load_kernel(name, ctx):
     assert rel(out[1][1], out[0][1]) <= 1e-9
     assert abs(out[1][2] - out[0][2]) <= 3
     assert misfit_err(out[1][0], ref) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", [D.PREC_FP64, D.PREC_MIXED])
+def test_widest_block_fields(prec, ctx):
+    """The widest block the library accepts, 512 + 512 columns (32-column TMA tiles in
+    the mixed path, one column per thread in the FP64 path), against the oracle's
+    solves of the same right-hand sides; the misfit from those fields."""
+    wl = synth.small_workload(8, 8, 4, 0.3, omega_nu=0.4, src_grid=(4, 4), det_grid=(4, 4), ls=512, ld=512, m0=3,
+                              sampling="gaussian", seed_index=72)
+    pb = problem.build(wl)
+    configure(ctx, pb, p=pb.inp.p0, prec=prec, rtol=1e-13)
+    f, rc = D.dot_misfit(ctx)
+    assert rc == D.DOT_OK
+    st = D.dot_get_stats(ctx)
+    assert st["k"] == 1024 and st["relres_max"] <= 1e-13
+    if prec == D.PREC_MIXED:
+        assert st["tuned_tma"] == 1
+    U, Z = D.dot_get_fields(ctx, wl.n, wl.ls, wl.ld, True)
+    mu = pb.mu_of(pb.inp.p0)
+    A = orc.assemble(pb.D, mu, wl.nx, wl.ny, wl.nz, wl.h, wl.bc, wl.omega_nu)
+    U_ref = orc.solve(A, pb.Bd @ pb.inp.W)
+    Z_ref = orc.solve(A, pb.Cd @ pb.inp.V)
+    assert rel(U, U_ref) <= 1e-10 and rel(Z, Z_ref) <= 1e-10
+    S = (pb.Cd @ pb.inp.V).T @ U_ref
+    R_s = S - pb.inp.V.T @ pb.M @ pb.inp.W
+    f_ref = float(np.sum(np.abs(R_s) ** 2))
+    assert abs(f - f_ref) <= 1e-8 * max(f_ref, 2.0 * np.linalg.norm(R_s) * np.linalg.norm(S))
