@@ -239,6 +239,15 @@ int dot_get_kernel_timing(dot_ctx* ctx, dot_kernel_timing* out);
  * The 7-point stencil of the block solve, exposed for testing. */
 int dot_apply(dot_ctx* ctx, int k, const double* x, double* y);
 
+/* Self-test of the device-side bounded waits (no counterpart in the paper): one warp
+ * waits on an mbarrier that nothing ever arrives at, with a budget of budget_cycles
+ * SM clock cycles (0 .. 4e9; the stencil kernels use about 4e9, roughly 2 s), gives
+ * up, and reports through the same kind of device error word the stencil kernels use.
+ * Nothing is in flight when the wait gives up.  Returns DOT_ETIMEOUT (the expected
+ * outcome), DOT_EBREAKDOWN if the wait claimed completion, DOT_EINVAL / DOT_ECUDA
+ * otherwise.  The context stays usable afterwards. */
+int dot_probe_wait(dot_ctx* ctx, int64_t budget_cycles);
+
 /* Allocation-free restriction and misfit (this library's addition; the paper has
  * no counterpart).  For callers that cannot let the library allocate device memory:
  * a latency-critical loop that must not stall on cudaMalloc / cudaFree (which can

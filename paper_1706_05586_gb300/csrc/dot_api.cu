@@ -1334,4 +1334,22 @@ int dot_apply(dot_ctx* c, int k, const double* x, double* y) {
     return rc;
 }
 
+int dot_probe_wait(dot_ctx* c, int64_t budget_cycles) {
+    if (!c) return fail(DOT_EINVAL, "null context");
+    if (budget_cycles < 0 || budget_cycles > 4000000000LL)
+        return fail(DOT_EINVAL, "budget_cycles must lie in [0, 4e9]");
+    DevBuf word;
+    TRY(ensure(word, 16));
+    int err = 0;
+    cudaError_t e = cudaMemsetAsync(word.p, 0, 16, c->s);
+    if (e == cudaSuccess) e = wait_probe(word.as<int>(), (long long)budget_cycles, c->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_flag, word.p, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e == cudaSuccess) err = c->h_flag[0];
+    release(word);
+    if (e != cudaSuccess) return fail(DOT_ECUDA, std::string("dot_probe_wait: ") + cudaGetErrorString(e));
+    if (err) return fail(DOT_ETIMEOUT, "dot_probe_wait: the bounded wait gave up after its budget, as intended");
+    return fail(DOT_EBREAKDOWN, "dot_probe_wait: a wait that nothing completes reported completion");
+}
+
 }  // extern "C"

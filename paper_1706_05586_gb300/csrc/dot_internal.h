@@ -86,6 +86,8 @@ struct TmaStencil {
     size_t smem = 0;
 };
 bool tma_stencil_eligible(ElemKind inner, int nx, int ny, int kp);
+// Launch the bounded-wait self-test: *err (device) becomes 1 when the wait gave up.
+cudaError_t wait_probe(int* err, long long budget, cudaStream_t s);
 cudaError_t tma_stencil_prepare(ElemKind inner, const DirRing& ring, const void* cf, int nx, int ny, int nz, int kp,
                                 int num_sms, TmaStencil* out);
 // q = A p for the direction in ring slot `slot` (its alpha goes to row `slot` of the

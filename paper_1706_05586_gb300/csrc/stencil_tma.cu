@@ -52,7 +52,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 }
 
 // Bounded wait for the given phase parity; false if the budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget = kWaitCycles) {
     const uint32_t addr = smem_u32(bar);
     const long long t0 = clock64();
     while (true) {
@@ -65,7 +65,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             : "r"(addr), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > budget) return false;
     }
 }
 
@@ -248,6 +248,25 @@ __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __gr
         __syncthreads();
         publish_counts(st, kp);
     }
+}
+
+// Self-test of the bounded wait: one mbarrier that nothing ever arrives at, waited on
+// with a budget of `budget` cycles by one warp; the wait must give up and report.
+// Nothing is in flight, so giving up leaves no copy behind.
+__global__ void k_wait_probe(int* err, long long budget) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0u, budget);
+    if (!__syncthreads_or(ok) && threadIdx.x == 0) *err = 1;
+}
+
+cudaError_t wait_probe(int* err, long long budget, cudaStream_t s) {
+    k_wait_probe<<<1, 32, 0, s>>>(err, budget);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------- host

@@ -57,6 +57,7 @@ SIGNATURES = {
     "dot_get_fields": [C.c_void_p, C.c_void_p, C.c_void_p],
     "dot_get_stats": [C.c_void_p, C.c_void_p],
     "dot_apply": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "dot_probe_wait": [C.c_void_p, C.c_int64],
     "dot_set_kernel_timing": [C.c_void_p, C.c_int],
     "dot_set_stencil_path": [C.c_void_p, C.c_int],
     "dot_set_launch_options": [C.c_void_p, C.c_int, C.c_int],
@@ -336,6 +337,11 @@ def dot_apply(ctx, X, cplx):
     Y = np.zeros_like(X, order="F")
     _check(load().dot_apply(ctx, X.shape[1], _ptr(X), _ptr(Y)))
     return Y
+
+
+def dot_probe_wait(ctx, budget_cycles, allow=(DOT_ETIMEOUT,)):
+    """Self-test of the bounded device waits; returns the status (DOT_ETIMEOUT expected)."""
+    return _check(load().dot_probe_wait(ctx, int(budget_cycles)), allow)
 
 
 def dot_restrict_misfit_noalloc(X, n, kp, ls, ld, colptrC, rowsC, valsC, nd, V, P, is_complex, S, Rs, f,
