@@ -175,6 +175,11 @@ int dot_forward_model(dot_ctx* ctx, double* M);
  * or (N doubles) with respect to mu after dot_set_mua.  g = 2 Re J^T conj(vec R_s)
  * with J the sampled Jacobian of Eq. (Jacobian kth column). */
 int dot_gradient(dot_ctx* ctx, double* f, double* g);
+/* dot_gradient with device outputs: f_dev (1 double) and g_dev (as for g) are device
+ * pointers of the context's device; they are written on the context's stream, which
+ * has completed when the call returns.  Lets a framework keep the gradient on the
+ * device (no host round trip). */
+int dot_gradient_dev(dot_ctx* ctx, double* f_dev, double* g_dev);
 /* Sampled mu-Jacobian J_mu[(l + ld i), v] = -Z_l[v] U_i[v]  ((ls*ld) x N,
  * column-major; complex interleaved when omega != 0).  (ls*ld*N) values. */
 int dot_jacobian_mua(dot_ctx* ctx, double* J);

@@ -5,7 +5,8 @@ forward pass runs the block solve of the forward and adjoint columns; the librar
 keeps both field blocks on the device (checkpointed), so the hand-written backward
 is the adjoint-field sensitivity g_mu = -2 Re sum conj(R_s) Z_l U_i followed by the
 PaLS chain rule g_p = (dmu/dp)^T g_mu (Eq. (Jacobiancomp), Eq. (UnbiasedGrad)),
-without a second solve.  With recompute=True the fields are solved again in the
+without a second solve; for CUDA tensors the gradient is written to device memory
+directly (dot_gradient_dev).  With recompute=True the fields are solved again in the
 backward pass instead (the state is invalidated after the forward), for callers that
 reuse the context for other work in between.
 
@@ -80,10 +81,17 @@ class DotMisfit(torch.autograd.Function):
             keep = _set_p(ctx.handle, p, ctx.consts)
         else:
             keep = None
-        _, g, _ = D.dot_gradient(ctx.handle, p.numel())
+        if p.is_cuda:
+            # the gradient stays on the device: the library writes it there directly
+            f_d = torch.empty(1, dtype=torch.float64, device=p.device)
+            g_d = torch.empty(p.numel(), dtype=torch.float64, device=p.device)
+            D.dot_gradient_dev(ctx.handle, f_d.data_ptr(), g_d.data_ptr())
+            g = g_d.to(p.dtype)
+        else:
+            _, g, _ = D.dot_gradient(ctx.handle, p.numel())
+            g = torch.from_numpy(np.asarray(g)).to(dtype=p.dtype)
         del keep
         _cached[_key(ctx.handle)] = ctx.token
-        g = torch.from_numpy(np.asarray(g)).to(device=p.device, dtype=p.dtype)
         return grad_out * g, None, None, None
 
 

@@ -1013,7 +1013,11 @@ int dot_measurements(dot_ctx* c, double* S) {
     return DOT_OK;
 }
 
-int dot_gradient(dot_ctx* c, double* f, double* g) {
+}  // extern "C"
+
+namespace {
+// dot_gradient and dot_gradient_dev: kind says where f and g live.
+int gradient_impl(dot_ctx* c, double* f, double* g, cudaMemcpyKind kind) {
     TRY(need_grid(c));
     if (!f || !g) return fail(DOT_EINVAL, "null output");
     if (!c->M_set) return fail(DOT_ESTATE, "dot_set_data has not been called");
@@ -1027,11 +1031,11 @@ int dot_gradient(dot_ctx* c, double* f, double* g) {
         CK(pals_chain_gp(c->p.as<double>(), c->m0, c->gamma, c->nx, c->ny, c->nz, c->h, c->wdmu.as<double>(),
                          c->gmu.as<double>(), c->gp.as<double>(), c->s));
         count(c, 1);
-        CK(cudaMemcpyAsync(g, c->gp.p, (size_t)5 * c->m0 * 8, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(g, c->gp.p, (size_t)5 * c->m0 * 8, kind, c->s));
     } else {
-        CK(cudaMemcpyAsync(g, c->gmu.p, c->n * 8, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(g, c->gmu.p, c->n * 8, kind, c->s));
     }
-    CK(cudaMemcpyAsync(f, c->f.p, 8, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(f, c->f.p, 8, kind, c->s));
     CK(cudaEventRecord(c->ev[2], c->s));
     CK(cudaStreamSynchronize(c->s));
     float ms = 0;
@@ -1039,6 +1043,15 @@ int dot_gradient(dot_ctx* c, double* f, double* g) {
     c->stats.ms_post = ms;
     if (c->fields_status != DOT_OK) return fail(c->fields_status, "block solve did not converge in every column");
     return DOT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int dot_gradient(dot_ctx* c, double* f, double* g) { return gradient_impl(c, f, g, cudaMemcpyDeviceToHost); }
+
+int dot_gradient_dev(dot_ctx* c, double* f_dev, double* g_dev) {
+    return gradient_impl(c, f_dev, g_dev, cudaMemcpyDeviceToDevice);
 }
 
 int dot_forward_model(dot_ctx* c, double* M) {

@@ -51,6 +51,7 @@ SIGNATURES = {
     "dot_measurements": [C.c_void_p, C.c_void_p],
     "dot_forward_model": [C.c_void_p, C.c_void_p],
     "dot_gradient": [C.c_void_p, C.c_void_p, C.c_void_p],
+    "dot_gradient_dev": [C.c_void_p, C.c_void_p, C.c_void_p],
     "dot_jacobian_mua": [C.c_void_p, C.c_void_p],
     "dot_jacobian_p": [C.c_void_p, C.c_void_p],
     "dot_get_mua": [C.c_void_p, C.c_void_p],
@@ -246,6 +247,12 @@ def dot_gradient(ctx, ng, allow=()):
     g = np.zeros(ng)
     rc = _check(load().dot_gradient(ctx, _ptr(f), _ptr(g)), allow)
     return float(f[0]), g, rc
+
+
+def dot_gradient_dev(ctx, f_ptr, g_ptr, allow=()):
+    """dot_gradient into device memory: f_ptr, g_ptr are device addresses (e.g. the
+    data_ptr() of float64 CUDA tensors of 1 and n_p elements)."""
+    return _check(load().dot_gradient_dev(ctx, C.c_void_p(f_ptr), C.c_void_p(g_ptr)), allow)
 
 
 def dot_jacobian_mua(ctx, ls, ld, n, cplx, allow=()):

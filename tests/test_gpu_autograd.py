@@ -90,3 +90,22 @@ def test_autograd_128cubed_directional_difference():
         assert abs((fp - fm) / (2 * eps) - g @ d) <= 1e-4 * np.linalg.norm(g)
     finally:
         D.dot_destroy(h)
+
+
+def test_gradient_dev_equals_host_outputs():
+    wl = synth.small_workload(16, 16, 9, 0.3, src_grid=(4, 4), det_grid=(4, 4), ls=16, ld=16, m0=4,
+                              sampling="gaussian", seed_index=66)
+    pb = problem.build(wl)
+    h = D.dot_create(0)
+    try:
+        configure(h, pb, p=pb.inp.p0, prec=D.PREC_MIXED, rtol=1e-12)
+        f, g, _ = D.dot_gradient(h, wl.np_)
+        f_d = torch.empty(1, dtype=torch.float64, device="cuda")
+        g_d = torch.empty(wl.np_, dtype=torch.float64, device="cuda")
+        assert D.dot_gradient_dev(h, f_d.data_ptr(), g_d.data_ptr()) == D.DOT_OK
+        assert f_d.item() == f and np.array_equal(g_d.cpu().numpy(), g)
+        with pytest.raises(D.DotError) as e:
+            D.dot_gradient_dev(h, 0, g_d.data_ptr())
+        assert e.value.code == D.DOT_EINVAL
+    finally:
+        D.dot_destroy(h)
