@@ -377,22 +377,25 @@ __global__ void __launch_bounds__(MT) k_dir(Op<T> op, const T* __restrict__ r, c
 // written for a column cannot reach x~.  When every slot holds a correction for one
 // of the thread's columns (the common case) all H loads are issued back to back.
 template <typename T, int H, int MT>
-__global__ void __launch_bounds__(MT) k_flush(const T* __restrict__ ring, int64_t slot_elems,
+__global__ void __launch_bounds__(MT, MT == 256 ? 2 : 1) k_flush(const T* __restrict__ ring, int64_t slot_elems,
                                                T* __restrict__ x, int64_t n, int kp, int slots, ColState st) {
     constexpr int W = Vec16<T>::W;
     const int tpv = kp / W;
     const int t = threadIdx.x % tpv, slot = threadIdx.x / tpv, c0 = t * W;
+    static_assert(H * W <= 32, "one mask bit per (slot, column)");
     T al[H][W];
-    bool on[H][W];
+    unsigned on = 0;   // bit j W + u: column c0 + u has a correction in slot j
     unsigned use = 0;  // bit j: some column of this thread has a correction in slot j
 #pragma unroll
     for (int j = 0; j < H; ++j) {
 #pragma unroll
         for (int u = 0; u < W; ++u) {
             const double2 a = st.alpha_hist[(int64_t)j * kp + c0 + u];
-            on[j][u] = a.x != 0.0 || a.y != 0.0;
             al[j][u] = enarrow<T>(a);
-            if (on[j][u]) use |= 1u << j;
+            if (a.x != 0.0 || a.y != 0.0) {
+                on |= 1u << (j * W + u);
+                use |= 1u << j;
+            }
         }
     }
     if (!use) return;
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(MT) k_flush(const T* __restrict__ ring, int64_
         for (int j = 0; j < H; ++j)
 #pragma unroll
             for (int u = 0; u < W; ++u)
-                if (on[j][u]) xv.e[u] = eadd(xv.e[u], emul(al[j][u], pv[j].e[u]));
+                if (on & (1u << (j * W + u))) xv.e[u] = eadd(xv.e[u], emul(al[j][u], pv[j].e[u]));
         st16(x + e, xv);
     }
 }
