@@ -80,7 +80,7 @@ struct DirRing {
 struct TmaStencil {
     alignas(64) unsigned char tmap[kDirRingMax][128];  // CUtensorMap of each ring slot
     alignas(64) unsigned char tmap_cf[128];  // CUtensorMap of the packed coefficients
-    int kc = 32;                          // columns per tile (32, or 16)
+    int kc = 32;                          // columns per tile (64 for FP32, 32, or 16)
     int zc = 0;                           // z planes per work item
     int grid = 0;
     size_t smem = 0;

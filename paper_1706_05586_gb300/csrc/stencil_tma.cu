@@ -2,7 +2,8 @@
 //
 // The 7-point operator of Sec. 2 (Eq. (PDE), Eq. (Eq:compmeas)) is applied to a
 // block of right-hand-side columns.  A CTA owns a tile of 8 x 8 cells x KC columns
-// (KC = 32, or 16 when the block width is an odd multiple of 16)
+// (KC = 32, or 16 when the block width is an odd multiple of 16; FP32 blocks whose
+// width is a multiple of 64 take KC = 64 with two columns per lane)
 // and marches it through a range of z planes.  Each plane of the tile, with a
 // one-cell halo in x and y, is brought into shared memory by two
 // cp.async.bulk.tensor loads completing on one mbarrier: the p values (4-D tensor
@@ -12,9 +13,10 @@
 // z neighbours are the adjacent planes of the ring, and the inner loop reads only
 // shared memory.  Out-of-range halo cells are zero-filled by the copy engine, p and
 // coefficients alike, so boundary faces contribute exact zeros without branches.
-// A warp owns one tile row; with KC = 32 a lane owns one column, with KC = 16 a
-// half-warp owns one cell, so every shared-memory read and global store of a warp is
-// one contiguous 256-byte (complex64) or 128-byte (FP32) run.
+// A warp owns one tile row; a lane owns one column (two adjacent FP32 columns in
+// 64-column tiles), and with KC = 16 a half-warp owns one cell, so every shared-memory
+// read and global store of a warp is one contiguous 256-byte (complex64, FP32 pairs)
+// or 128-byte run.
 //
 // Every wait on an mbarrier is bounded by a clock budget; on expiry the CTA records
 // an error code, drains its outstanding copies (again bounded) and stops issuing work.
@@ -89,6 +91,31 @@ __device__ __forceinline__ void tma_plane(const CUtensorMap* tm, const CUtensorM
     tma_load4(tc, dst + p_bytes, bar, 0, x, y, z);
 }
 
+// Two adjacent real columns carried by one lane (FP32 tiles of 64 columns, so that a
+// warp moves 256-byte rows as in the complex64 tiles).  Componentwise arithmetic.
+struct alignas(8) RPair {
+    float a, b;
+};
+__device__ __forceinline__ RPair escale(float s, RPair x) { return RPair{s * x.a, s * x.b}; }
+__device__ __forceinline__ RPair eadd(RPair x, RPair y) { return RPair{x.a + y.a, x.b + y.b}; }
+__device__ __forceinline__ RPair esub(RPair x, RPair y) { return RPair{x.a - y.a, x.b - y.b}; }
+__device__ __forceinline__ RPair emul(RPair x, RPair y) { return RPair{x.a * y.a, x.b * y.b}; }
+__device__ __forceinline__ double2 ewide(RPair x) { return make_double2(x.a, x.b); }
+
+// What a lane carries in a tile of KC columns of element type T: L, covering CPL columns.
+template <typename T, int KC>
+struct TmaLane {
+    using L = T;
+    static constexpr int CPL = 1;
+    static __device__ __forceinline__ L zero() { return ezero<T>(); }
+};
+template <>
+struct TmaLane<float, 64> {
+    using L = RPair;
+    static constexpr int CPL = 2;
+    static __device__ __forceinline__ L zero() { return RPair{0.f, 0.f}; }
+};
+
 }  // namespace
 
 // Shared memory: NBUF ring slots (a plane of p, then its coefficients), NBUF
@@ -101,6 +128,10 @@ __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __gr
                                                        T* __restrict__ q, int kp, int zc_len, ColState st,
                                                        int hslot) {
     using R = typename Elem<T>::R;
+    using Lane = TmaLane<T, KC>;
+    using L = typename Lane::L;
+    constexpr int CPL = Lane::CPL;       // columns per lane
+    constexpr int LPC = KC / CPL;        // lanes per cell
     constexpr int PLANE = KC * HX * HY;  // elements
     constexpr int P_BYTES = PLANE * sizeof(T);
     constexpr int SLOT = P_BYTES + CF_SLOT;
@@ -111,11 +142,11 @@ __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __gr
     double2* acc = reinterpret_cast<double2*>(bar + NBUF);  // NBUF even: 16-byte aligned
     double2* wsum = reinterpret_cast<double2*>(base);
     static_assert(NBUF % 2 == 0, "accumulator alignment");
-    static_assert(KC == 16 || KC == 32, "column tile");
-    constexpr int XS = 32 / KC;  // cells per warp instruction
+    static_assert(LPC == 16 || LPC == 32, "column tile");
+    constexpr int XS = 32 / LPC;  // cells per warp instruction
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int col = lane % KC, xsub = lane / KC;
+    const int col = lane % LPC, xsub = lane / LPC;
     const int nx = op.nx, ny = op.ny, nz = op.nz;
     const int tiles_x = nx / TX, tiles_y = ny / TY, tiles_c = kp / KC;
     const int zchunks = (nz + zc_len - 1) / zc_len;
@@ -142,8 +173,13 @@ __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __gr
         const int zci = rem / tiles_c;
         const int i0 = txi * TX, j0 = tyi * TY, c0 = cci * KC;
         const int z0 = zci * zc_len, z1 = min(z0 + zc_len, nz);
-        const int c = c0 + col;
-        const bool run = st.active[c] && !st.upd[c];
+        // the lane's columns c0 + CPL col .. c0 + CPL col + CPL - 1
+        bool run = false;
+#pragma unroll
+        for (int u = 0; u < CPL; ++u) {
+            const int cu = c0 + CPL * col + u;
+            run = run || (st.active[cu] && !st.upd[cu]);
+        }
         if (!__syncthreads_or(run)) continue;
 
         // planes z0-1 .. z1 go to buffers (z - z0 + 1) mod NBUF
@@ -164,7 +200,7 @@ __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __gr
             }
         }
         failed = __syncthreads_or(!ok);
-        T pq = ezero<T>();
+        L pq = Lane::zero();
         for (int k = z0; k < z1 && !failed; ++k) {
             if (k + 2 <= z1) {
                 const int b = slot(k + 2);
@@ -184,33 +220,33 @@ __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __gr
             if (failed) break;
             const unsigned char* sm = base + (size_t)slot(k - 1) * SLOT;
             const unsigned char* sc = base + (size_t)slot(k) * SLOT;
-            const T* pm = reinterpret_cast<const T*>(sm);
-            const T* pc = reinterpret_cast<const T*>(sc);
-            const T* pn = reinterpret_cast<const T*>(base + (size_t)slot(k + 1) * SLOT);
+            const L* pm = reinterpret_cast<const L*>(sm);
+            const L* pc = reinterpret_cast<const L*>(sc);
+            const L* pn = reinterpret_cast<const L*>(base + (size_t)slot(k + 1) * SLOT);
             const Cf4<R>* cm = reinterpret_cast<const Cf4<R>*>(sm + P_BYTES);
             const Cf4<R>* cc = reinterpret_cast<const Cf4<R>*>(sc + P_BYTES);
             const int j = j0 + warp;
-            const int row = (warp + 1) * HX * KC;
+            const int row = (warp + 1) * HX * LPC;
             const int crow = (warp + 1) * HX;
 #pragma unroll 2
             for (int xi = xsub; xi < TX; xi += XS) {
                 const int i = i0 + xi;
                 const int v = i + nx * (j + ny * k);
-                const int o = row + (xi + 1) * KC + col;
+                const int o = row + (xi + 1) * LPC + col;
                 const int co = crow + xi + 1;
                 const Cf4<R> cv = cc[co];
-                const T xc = pc[o];
-                T a = escale(cv.dre, xc);
-                if (Elem<T>::cplx) a = eadd(a, emul_i(op.w, xc));
+                const L xc = pc[o];
+                L a = escale(cv.dre, xc);
+                if constexpr (Elem<T>::cplx) a = eadd(a, emul_i(op.w, xc));
                 // faces to the -x, -y, -z neighbours carry that neighbour's coefficient
                 // (zero outside the grid, where p is zero as well)
-                a = esub(a, escale(cc[co - 1].cx, pc[o - KC]));
-                a = esub(a, escale(cv.cx, pc[o + KC]));
-                a = esub(a, escale(cc[co - HX].cy, pc[o - HX * KC]));
-                a = esub(a, escale(cv.cy, pc[o + HX * KC]));
+                a = esub(a, escale(cc[co - 1].cx, pc[o - LPC]));
+                a = esub(a, escale(cv.cx, pc[o + LPC]));
+                a = esub(a, escale(cc[co - HX].cy, pc[o - HX * LPC]));
+                a = esub(a, escale(cv.cy, pc[o + HX * LPC]));
                 a = esub(a, escale(cm[co].cz, pm[o]));
                 a = esub(a, escale(cv.cz, pn[o]));
-                q[(int64_t)v * kp + c] = a;
+                reinterpret_cast<L*>(q + (int64_t)v * kp + c0)[col] = a;
                 pq = eadd(pq, emul(xc, a));
             }
             __syncthreads();  // plane k-1's buffer is refilled in the next iteration
@@ -221,14 +257,22 @@ __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __gr
         wsum[warp * 32 + lane] = ewide(pq);
         __syncthreads();
         if (threadIdx.x < KC) {
+            // column t is component t % CPL of lane t / CPL (a complex lane carries
+            // one column as (re, im); a pair lane two real columns)
+            const int t = threadIdx.x, lt = t / CPL, comp = t % CPL;
             double2 s = make_double2(0.0, 0.0);
             for (int w = 0; w < TY; ++w)
                 for (int h = 0; h < XS; ++h) {
-                    s.x += wsum[w * 32 + h * KC + threadIdx.x].x;
-                    s.y += wsum[w * 32 + h * KC + threadIdx.x].y;
+                    const double2 pw = wsum[w * 32 + h * LPC + lt];
+                    if (CPL == 1) {
+                        s.x += pw.x;
+                        s.y += pw.y;
+                    } else {
+                        s.x += comp ? pw.y : pw.x;
+                    }
                 }
-            acc[c0 + threadIdx.x].x += s.x;
-            acc[c0 + threadIdx.x].y += s.y;
+            acc[c0 + t].x += s.x;
+            acc[c0 + t].y += s.y;
         }
         __syncthreads();
     }
@@ -306,7 +350,8 @@ cudaError_t tma_stencil_prepare(ElemKind inner, const DirRing& ring, const void*
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const size_t es = inner == EK_C64 ? 8 : 4;
-    const int kc = kp % 32 == 0 ? 32 : 16;
+    // FP32: 64-column tiles (two columns per lane) when the block width allows
+    const int kc = (inner == EK_F32 && kp % 64 == 0) ? 64 : (kp % 32 == 0 ? 32 : 16);
     const cuuint64_t dims[4] = {(cuuint64_t)kp, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     const cuuint64_t strides[3] = {(cuuint64_t)kp * es, (cuuint64_t)kp * nx * es, (cuuint64_t)kp * nx * ny * es};
     const cuuint32_t box[4] = {(cuuint32_t)kc, HX, HY, 1};
@@ -335,6 +380,8 @@ cudaError_t tma_stencil_prepare(ElemKind inner, const DirRing& ring, const void*
     cudaError_t e;
     if (inner == EK_C64)
         e = kc == 32 ? tma_configure<float2, 32>(out->smem, &per_sm) : tma_configure<float2, 16>(out->smem, &per_sm);
+    else if (kc == 64)
+        e = tma_configure<float, 64>(out->smem, &per_sm);
     else
         e = kc == 32 ? tma_configure<float, 32>(out->smem, &per_sm) : tma_configure<float, 16>(out->smem, &per_sm);
     if (e != cudaSuccess) return e;
@@ -386,7 +433,9 @@ cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil&
         op.nx = o.nx;
         op.ny = o.ny;
         op.nz = o.nz;
-        if (t.kc == 32)
+        if (t.kc == 64)
+            k_pq_tma<float, 64><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st, slot);
+        else if (t.kc == 32)
             k_pq_tma<float, 32><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st, slot);
         else
             k_pq_tma<float, 16><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st, slot);

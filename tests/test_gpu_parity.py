@@ -49,6 +49,9 @@ CASES = {
                                              ls=24, ld=24, m0=5, sampling="gaussian", seed_index=67),
     "real_24x8x7_k16": synth.small_workload(24, 8, 7, 0.3, src_grid=(3, 3), det_grid=(3, 3), ls=8, ld=8,
                                             m0=4, sampling="gaussian", seed_index=68),
+    # real block of 64 columns: the FP32 TMA stencil with 64-column tiles, two columns per lane
+    "real_16x8x5_k64": synth.small_workload(16, 8, 5, 0.3, src_grid=(6, 6), det_grid=(6, 6), ls=32, ld=32, m0=4,
+                                            sampling="gaussian", seed_index=74),
     # degenerate depth: a single layer of cells (no z neighbours), TMA path
     "real_16x16x1_k32": synth.small_workload(16, 16, 1, 0.3, src_grid=(4, 4), det_grid=(4, 4), ls=16, ld=16,
                                              m0=4, sampling="gaussian", seed_index=69),
@@ -257,7 +260,7 @@ def test_forward_model_all_sources(name, ctx):
 
 
 @pytest.mark.parametrize("name", ["cplx_24x16x10_k32", "real_16x16x9_k32", "cplx_16x24x8_k48", "real_24x8x7_k16",
-                                  "real_16x16x1_k32", "cplx_8x8x6_k256"])
+                                  "real_16x16x1_k32", "cplx_8x8x6_k256", "real_16x8x5_k64"])
 def test_tma_stencil_matches_direct_load_kernel(name, ctx):
     """The TMA-staged stencil and the direct-load stencil give the same solve to rounding."""
     pb, ref = _case(name)
