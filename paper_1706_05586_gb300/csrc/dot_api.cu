@@ -387,6 +387,10 @@ int apply_tuning(dot_ctx* c, SolveRun& r, const Tuning& t) {
     const int64_t need = (r.n + r.Lv.slots - 1) / r.Lv.slots;
     const int64_t g = (int64_t)c->num_sms * t.blocks_per_sm;
     r.Lv.grid = (int)std::max<int64_t>(1, std::min(need, g));
+    // the flush holds 8 directions per thread: two 256-thread blocks (one 1024-thread
+    // block) fit per SM, so it runs one full wave of those
+    const int64_t gf = (int64_t)c->num_sms * (r.Lv.threads > 256 ? 1 : 2);
+    r.ring.flush_grid = (int)std::max<int64_t>(1, std::min(need, gf));
     if (t.tma && !r.tma_ready) {
         CK(tma_stencil_prepare(r.inner, r.ring, c->cf32.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma));
         r.tma_ready = true;
@@ -430,13 +434,13 @@ int solve_begin(dot_ctx* c, int kp, int kr) {
     r.delta = r.mixed ? c->delta : 0.0;
     r.maxit = c->maxit > 0 ? c->maxit : 10 * (c->nx + c->ny + c->nz);
     const bool tma_ok = tma_stencil_eligible(r.inner, c->nx, c->ny, kp);
-    Tuning base{c->use_tma && tma_ok, 4};  // four 256-thread blocks per SM: one wave, ample bytes in flight
+    Tuning base{c->use_tma && tma_ok, 5};  // five 256-thread blocks per SM: one wave at the update kernel's register limit
     if (c->autotune) {
         const bool have = c->tuned.valid && c->tuned.n == r.n && c->tuned.kp == kp && c->tuned.inner == (int)r.inner;
         if (have) {
             base = Tuning{c->tuned.tma && tma_ok, c->tuned.blocks_per_sm};
         } else {
-            for (int bps : {4, 8, 16}) {
+            for (int bps : {4, 5, 8, 16}) {
                 r.cands.push_back(Tuning{false, bps});
                 if (tma_ok) r.cands.push_back(Tuning{true, bps});
             }

@@ -75,6 +75,7 @@ struct DirRing {
     void* base = nullptr;    // H consecutive slots of n x kp recurrence-type elements
     int64_t slot_elems = 0;  // elements per slot
     int H = 0;               // slots in use: 8, 4 or 2 (a divisor of the poll batch)
+    int flush_grid = 0;      // blocks of the flush: one wave at its register limit (0: as the others)
 };
 
 struct TmaStencil {

@@ -681,20 +681,21 @@ cudaError_t kry_step(ElemKind inner, const OpRaw& o, void* x, void* r, const Dir
         if (slot == H - 1) {
             const T* rb = base;
             const int64_t se = ring.slot_elems;
+            const int fg = ring.flush_grid > 0 ? ring.flush_grid : Lv.grid;
             if (wide) {
                 if (H == 8)
-                    k_flush<T, 8, 1024><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+                    k_flush<T, 8, 1024><<<fg, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
                 else if (H == 4)
-                    k_flush<T, 4, 1024><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+                    k_flush<T, 4, 1024><<<fg, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
                 else
-                    k_flush<T, 2, 1024><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+                    k_flush<T, 2, 1024><<<fg, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
             } else {
                 if (H == 8)
-                    k_flush<T, 8, 256><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+                    k_flush<T, 8, 256><<<fg, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
                 else if (H == 4)
-                    k_flush<T, 4, 256><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+                    k_flush<T, 4, 256><<<fg, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
                 else
-                    k_flush<T, 2, 256><<<Lv.grid, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
+                    k_flush<T, 2, 256><<<fg, Lv.threads, 0, s>>>(rb, se, (T*)x, n, kp, Lv.slots, st);
             }
             if (evf) record_timing(*evf, s);
         }
