@@ -129,7 +129,8 @@ __global__ void k_start_inner(Op<T> op, const T64* __restrict__ b, T* __restrict
 __device__ __forceinline__ bool running(const ColState& st, int c) { return st.active[c] && !st.upd[c]; }
 
 // Launch shape of the vectorised iteration kernels: kp / W threads per voxel, about
-// 256 threads per block, eight blocks per SM.
+// 256 threads per block, at most eight blocks per SM (the solver then sets the grid
+// from its blocks-per-SM choice).
 Launch vector_launch(int64_t n, int kp, int w, int num_sms) {
     Launch L;
     const int tpv = kp / w;
@@ -172,7 +173,8 @@ __device__ __forceinline__ void column_partials_w(const double2 (&a)[W], const d
 }
 
 // q = A p and pq = p^T q; finaliser alpha = rho / pq.  One 16-byte load per
-// neighbour moves W columns; the grid keeps eight blocks per SM in flight.
+// neighbour moves W columns (the direct-load form, for shapes the TMA stencil does not
+// take).
 template <typename T, int MT>
 __global__ void __launch_bounds__(MT) k_pq(Op<T> op, const T* __restrict__ p, T* __restrict__ q, int kp,
                                                int slots, ColState st, int hslot) {
