@@ -48,7 +48,7 @@ constexpr int kRefreshEvery = 256;
 // ------------------------------------------------------------- start of a solve
 // x64 = 0 and ||b||^2 per column; finaliser: scale s = ||b||, activity.
 template <typename T64>
-__global__ void k_start_norm(const T64* __restrict__ b, T64* __restrict__ x64, int64_t n, int kp, int slots,
+__global__ void __launch_bounds__(1024) k_start_norm(const T64* __restrict__ b, T64* __restrict__ x64, int64_t n, int kp, int slots,
                              ColState st, double rtol) {
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
     double bb = 0.0;
@@ -84,7 +84,7 @@ __global__ void k_start_norm(const T64* __restrict__ b, T64* __restrict__ x64, i
 
 // r~ = b / s, x~ = 0, p = M^{-1} r~; rho = r~^T M^{-1} r~, ||r~||^2.
 template <typename T, typename T64>
-__global__ void k_start_inner(Op<T> op, const T64* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
+__global__ void __launch_bounds__(1024) k_start_inner(Op<T> op, const T64* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
                               T* __restrict__ p, int64_t n, int kp, int slots, ColState st) {
     using R = typename Elem<T>::R;
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
@@ -127,6 +127,10 @@ __global__ void k_start_inner(Op<T> op, const T64* __restrict__ b, T* __restrict
 
 // -------------------------------------------------------------- one iteration
 __device__ __forceinline__ bool running(const ColState& st, int c) { return st.active[c] && !st.upd[c]; }
+
+// The one-column-per-thread kernels (start, promotion, true residual, refresh) run
+// blocks of kp x slots threads, up to 1024 at the widest block; they are compiled for
+// 1024 threads (at most 64 registers), so every block width stays launchable.
 
 // Launch shape of the vectorised iteration kernels: kp / W threads per voxel, about
 // 256 threads per block, at most eight blocks per SM (the solver then sets the grid
@@ -427,7 +431,7 @@ __global__ void __launch_bounds__(MT, MT == 256 ? 2 : 1) k_flush(const T* __rest
 // between batches, after the flush of the direction ring, so x~ holds every
 // correction made so far.
 template <typename T64, typename T>
-__global__ void k_promote(T64* __restrict__ x64, T* __restrict__ x, int64_t n, int kp, int slots, ColState st,
+__global__ void __launch_bounds__(1024) k_promote(T64* __restrict__ x64, T* __restrict__ x, int64_t n, int kp, int slots, ColState st,
                           int all) {
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
     if (!(all || st.active[c])) return;
@@ -483,7 +487,7 @@ __device__ __forceinline__ T residual_at(const Op<T>& op, const T* __restrict__ 
 }
 
 template <typename T64>
-__global__ void k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64* __restrict__ x64,
+__global__ void __launch_bounds__(1024) k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64* __restrict__ x64,
                                 T64* __restrict__ r64, int64_t n, int kp, int slots, ColState st, double rtol,
                                 int maxit, int all) {
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
@@ -537,7 +541,7 @@ __global__ void k_true_residual(Op<T64> op, const T64* __restrict__ b, const T64
 // direction is kept in the old scale, so beta = (rho' / rho_prev) / ratio carries it
 // over, where rho_prev is the rho of the iteration that produced the replaced residual.
 template <typename T, typename T64>
-__global__ void k_refresh(Op<T> op, const T64* __restrict__ r64, T* __restrict__ r, int64_t n, int kp, int slots,
+__global__ void __launch_bounds__(1024) k_refresh(Op<T> op, const T64* __restrict__ r64, T* __restrict__ r, int64_t n, int kp, int slots,
                           ColState st) {
     using R = typename Elem<T>::R;
     const int c = threadIdx.x % kp, slot = threadIdx.x / kp;
@@ -545,10 +549,12 @@ __global__ void k_refresh(Op<T> op, const T64* __restrict__ r64, T* __restrict__
     T rho = ezero<T>();
     R rr = 0;
     if (sel) {
-        const double inv = 1.0 / st.scale[c];
+        // scale after narrowing: in FP32 the product then runs on the FP32 pipe (this
+        // part's FP64 pipe is about 58 times slower); in FP64 it is the same operation
+        const R inv = (R)(1.0 / st.scale[c]);
         VOXEL_LOOP(v) {
             const int64_t e = v * kp + c;
-            const T rv = enarrow<T>(ewide(escale(inv, r64[e])));
+            const T rv = escale(inv, enarrow<T>(ewide(r64[e])));
             r[e] = rv;
             rho = eadd(rho, emul(rv, emul(op.dinv[v], rv)));
             rr += eabs2(rv);
