@@ -223,6 +223,13 @@ int dot_get_stats(dot_ctx* ctx, dot_stats* stats);
  * reduction order follows the launch shape, results then agree to rounding (not
  * bitwise) with an untuned run. */
 int dot_set_launch_options(dot_ctx* ctx, int graphs, int autotune);
+/* Slots of the direction ring (no counterpart in the paper): the search directions of
+ * the last `slots` iterations stay on the device and x~ takes their corrections in one
+ * pass per ring.  slots = 0 (default) tries 8, then 4, then 2 as device memory allows;
+ * 2, 4 or 8 caps the ring at that size.  Every size gives bitwise the same results
+ * (each correction is added in iteration order either way); smaller rings stream
+ * more bytes per iteration.  Errors: DOT_EINVAL for other values. */
+int dot_set_direction_ring(dot_ctx* ctx, int slots);
 /* Misfit and gradient of several contexts (independent inversions, e.g. uneven grids
  * and mixed omega) at once: their block solves advance in interleaved batches on
  * their own streams, so one context's host poll overlaps the others' kernels.  Same

@@ -200,6 +200,7 @@ struct dot_ctx {
     bool autotune = false;
     TunedChoice tuned;
     Tuning last_cfg{false, -1};  // launch configuration of the last solve (blocks_per_sm -1: none yet)
+    int ring_cap = kDirRingMax;  // most direction-ring slots to try (dot_set_direction_ring)
     cudaEvent_t bev[2] = {nullptr, nullptr};
 
     // kernel timing (dot_set_kernel_timing)
@@ -420,7 +421,7 @@ int solve_begin(dot_ctx* c, int kp, int kr) {
     // direction ring: as many slots (8, 4 or 2) as device memory allows
     const size_t slot_bytes = (size_t)r.n * kp * r.ei;
     r.ring = DirRing{};
-    for (int H = kDirRingMax; H >= 2; H /= 2) {
+    for (int H = c->ring_cap; H >= 2; H /= 2) {
         if (kPoll % H == 0 && try_ensure(c->pi, (size_t)H * slot_bytes)) {
             r.ring = DirRing{c->pi.p, (int64_t)r.n * kp, H};
             break;
@@ -1260,6 +1261,15 @@ int dot_set_launch_options(dot_ctx* c, int graphs, int autotune) {
     TRY(need_ctx(c));
     c->use_graphs = graphs != 0;
     c->autotune = autotune != 0;
+    invalidate_fields(c);
+    return DOT_OK;
+}
+
+int dot_set_direction_ring(dot_ctx* c, int slots) {
+    TRY(need_ctx(c));
+    if (slots != 0 && slots != 2 && slots != 4 && slots != 8)
+        return fail(DOT_EINVAL, "slots must be 0 (as many as memory allows), 2, 4 or 8");
+    c->ring_cap = slots == 0 ? kDirRingMax : slots;
     invalidate_fields(c);
     return DOT_OK;
 }

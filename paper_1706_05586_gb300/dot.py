@@ -62,6 +62,7 @@ SIGNATURES = {
     "dot_set_kernel_timing": [C.c_void_p, C.c_int],
     "dot_set_stencil_path": [C.c_void_p, C.c_int],
     "dot_set_launch_options": [C.c_void_p, C.c_int, C.c_int],
+    "dot_set_direction_ring": [C.c_void_p, C.c_int],
     "dot_gradient_batch": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "dot_optimized_sampling": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_int,
                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -310,6 +311,10 @@ def dot_symeig(A):
 
 def dot_set_launch_options(ctx, graphs=True, autotune=False):
     return _check(load().dot_set_launch_options(ctx, int(bool(graphs)), int(bool(autotune))))
+
+
+def dot_set_direction_ring(ctx, slots=0):
+    return _check(load().dot_set_direction_ring(ctx, int(slots)))
 
 
 def dot_gradient_batch(ctxs, ngs, allow=()):

@@ -137,3 +137,33 @@ def test_stats_report_the_launch_configuration(problems):
         tma_ok = pb.wl.nx % 8 == 0 and pb.wl.ny % 8 == 0 and kp % 16 == 0
         assert st["tuned_blocks_per_sm"] == 5
         assert st["tuned_tma"] == (1 if tma_ok else 0)
+
+
+@pytest.mark.parametrize("prec", [D.PREC_MIXED, D.PREC_FP64])
+def test_direction_ring_sizes_give_the_same_results(problems, prec):
+    # each correction alpha_j p_j reaches x~ in iteration order whatever the ring size
+    out = []
+    for slots in (8, 4, 2):
+        for pb in problems:
+            h = D.dot_create(0)
+            try:
+                configure(h, pb, p=pb.inp.p0, prec=prec, rtol=1e-12)
+                D.dot_set_direction_ring(h, slots)
+                f, g, _ = D.dot_gradient(h, pb.wl.np_)
+                out.append((slots, pb.wl.name, f, g, D.dot_get_stats(h)["iters_max"]))
+            finally:
+                D.dot_destroy(h)
+    ref = {name: (f, g, it) for s, name, f, g, it in out if s == 8}
+    for s, name, f, g, it in out:
+        f8, g8, it8 = ref[name]
+        assert f == f8 and np.array_equal(g, g8) and it == it8, (s, name)
+
+
+def test_direction_ring_rejects_other_sizes():
+    h = D.dot_create(0)
+    try:
+        with pytest.raises(D.DotError) as e:
+            D.dot_set_direction_ring(h, 3)
+        assert e.value.code == D.DOT_EINVAL
+    finally:
+        D.dot_destroy(h)
