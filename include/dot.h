@@ -273,15 +273,20 @@ int dot_probe_wait(dot_ctx* ctx, int64_t budget_cycles);
  *   X: block of fields over n cells, element (v, c) at v * kp + c (double, or
  *      interleaved complex when is_complex), kp >= ls, columns 0..ls-1 the forward
  *      fields U (further columns, e.g. the adjoint fields, are not read);
- *   colptrC (nd + 1, int64), rowsC, valsC: detectors C as CSC;  V: nd x ld column-major;
+ *   colptrC (nd + 1, int64), rowsC, valsC: detectors C as CSC, every rowsC entry a cell
+ *      index in [0, n) (not checked: the arrays stay on the device, and an index outside
+ *      the grid makes the restriction read outside X);  V: nd x ld column-major;
  *   P: l_d x l_s interleaved complex V^T M W, or NULL for no data (R_s = S);
  *   S, Rs: l_d x l_s interleaved complex outputs;  f: one double.
  * The only scratch, T, is a fixed device array of DOT_NOALLOC_MAX_T complex entries
  * (1 MiB) that every GPU loading the library holds until the process exits;
  * nd * ls above that limit is rejected with DOT_EINVAL.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress), so make it before any
- * stream capture.  All calls share the array, which keeps the last call's contents
- * (each call overwrites every entry it reads); calls that overlap on the GPU race. */
+ * stream capture; the address is kept for the life of the process, so do not use this
+ * entry point on a device after cudaDeviceReset (or any other teardown of its primary
+ * context) in the same process.  All calls share the array, which keeps the last call's
+ * contents (each call overwrites every entry it reads); calls that overlap on the GPU
+ * race. */
 #define DOT_NOALLOC_MAX_T 65536
 int dot_restrict_misfit_noalloc(const double* X, int64_t n, int kp, int ls, int ld, const int64_t* colptrC,
                                 const int32_t* rowsC, const double* valsC, int nd, const double* V,

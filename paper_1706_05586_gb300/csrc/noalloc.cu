@@ -28,7 +28,10 @@ int noalloc_fail(int code, const std::string& msg) { return dotk::record_error(c
 
 // Device address of the scratch array on the current device.  The name
 // g_noalloc_T is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached for the life of the process: a
+// cudaDeviceReset (or another teardown of the device's primary context) would leave
+// the cached address stale, which is why the entry point is documented as not usable
+// on a device after such a reset.
 int scratch_address(void** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);

@@ -48,3 +48,72 @@ def test_probe_rejects_bad_budget():
         assert e.value.code == D.DOT_EINVAL
     finally:
         D.dot_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [D.PREC_FP64, D.PREC_MIXED])
+def test_breakdown_is_reported_and_outputs_written(prec):
+    """A zero Jacobi diagonal breaks CG down at its first step (z = M^{-1} r is not finite):
+    a single cell with six Dirichlet faces, D = 1/2 and h = 1 gives each face exactly
+    2 D / h^2 = 1, so mu = -6 makes the diagonal exactly zero.  The solve stops the
+    column with DOT_EBREAKDOWN, the misfit is still written, and the same context then
+    evaluates a well-posed problem as before."""
+    h = D.dot_create(0)
+    try:
+        D.dot_set_grid(h, 1, 1, 1, 1.0, (synth.DIRICHLET,) * 6)
+        D.dot_set_omega(h, 0.0)
+        D.dot_set_diffusion(h, np.array([0.5]))
+        D.dot_set_mua(h, np.array([-6.0]))
+        one = (np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), np.array([1.0]))
+        D.dot_set_sources(h, one)
+        D.dot_set_detectors(h, one)
+        D.dot_set_data(h, np.array([[0.25]]))
+        D.dot_set_sampling(h, np.ones((1, 1)), np.ones((1, 1)))
+        D.dot_set_solver(h, prec, 1e-10, 0)
+        f, rc = D.dot_misfit(h, allow=(D.DOT_EBREAKDOWN,))
+        assert rc == D.DOT_EBREAKDOWN
+        assert f == pytest.approx(0.0625)          # S = C^T U = 0 with U = 0, R_s = -0.25
+        st = D.dot_get_stats(h)
+        assert st["status"] == D.DOT_EBREAKDOWN and st["iters_max"] == 0
+        # a positive diagonal: A = [1] (mu = -5), so U = 1, S = 1, f = (1 - 0.25)^2
+        D.dot_set_mua(h, np.array([-5.0]))
+        f, rc = D.dot_misfit(h)
+        assert rc == D.DOT_OK and f == pytest.approx(0.5625, rel=1e-12)
+    finally:
+        D.dot_destroy(h)
+
+
+def test_allocation_failure_is_reported_and_context_survives():
+    """Block vectors that cannot fit: 256 x 256 x 512 cells x 1,024 complex columns need
+    550 GB for the right-hand sides alone, more than the device holds.  The evaluation
+    fails at that allocation with DOT_ENOMEM before any solve, and the same context then
+    evaluates a small problem against the oracle."""
+    nx, ny, nz = 256, 256, 512
+    n = nx * ny * nz
+    big = synth.small_workload(nx, ny, nz, 8.0 / nx, omega_nu=synth.OMEGA_NU_100MHZ, src_grid=(4, 4),
+                               det_grid=(4, 4), ls=512, ld=512, m0=1, sampling="gaussian", seed_index=75)
+    inp = synth.draw(big)
+    h = D.dot_create(0)
+    try:
+        D.dot_set_grid(h, nx, ny, nz, big.h, big.bc)
+        D.dot_set_omega(h, big.omega_nu)
+        D.dot_set_diffusion(h, np.full(n, 1.0 / 30.0))
+        D.dot_set_mua(h, np.full(n, synth.MU_OUT))
+        D.dot_set_sources(h, inp.B)
+        D.dot_set_detectors(h, inp.C)
+        D.dot_set_data(h, np.zeros((big.nd, big.ns), dtype=complex))
+        D.dot_set_sampling(h, inp.W, inp.V)
+        D.dot_set_solver(h, D.PREC_MIXED, 1e-10, 0)
+        with pytest.raises(D.DotError) as e:
+            D.dot_misfit(h)
+        assert e.value.code == D.DOT_ENOMEM
+        assert "cudaMalloc" in D.dot_last_error()
+        assert D.dot_get_stats(h)["block_solves"] == 0
+        # the same context, now sized for a small problem
+        pb = problem.build(synth.small_workload(11, 6, 7, 0.35, omega_nu=0.3, src_grid=(3, 1), det_grid=(2, 2),
+                                                ls=3, ld=2, m0=5, sampling="gaussian", seed_index=62))
+        ref = pb.evaluate(pb.inp.p0)
+        configure(h, pb, p=pb.inp.p0, prec=D.PREC_FP64, rtol=2e-15)
+        f, rc = D.dot_misfit(h)
+        assert rc == D.DOT_OK and abs(f - ref["f"]) <= 1e-10 * ref["f"]
+    finally:
+        D.dot_destroy(h)

@@ -1,16 +1,21 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
-seeded inputs.
+seeded inputs, entry by entry.
 
-FP64 path: the GPU solves to rtol 1e-14 (the oracle solves directly) and every
-output must agree to 1e-10 relative (Frobenius norm of the difference over the
-norm of the oracle value).  A residual-based stop at 1e-13 is not enough: the
-measurements weight the far field of each column, where the relative error of a
-solve is larger than its residual suggests (measured: 1.4e-10 in S at rtol 1e-13
-on the 32x32x16 workload, 1.4e-11 at 1e-14).  Mixed precision (FP32 / complex64
-recurrence with FP64 reliable updates, true residual to 1e-13): 1e-8 relative.  The misfit is
-compared against max(f, 2 ||R_s|| ||S||) and the gradient against
-2 ||J|| (||R_s|| + ||S||) (gpu_setup.misfit_err, grad_err), because both are
-differences of nearly equal terms near the data.
+FP64 path: the GPU solves until the FP64 true residual ||b - A x|| <= 2e-15 ||b|| in
+every column (the oracle solves by sparse LU, whose own true residual is 0.5-1.7e-15
+on these cases) and every output must agree to 1e-10.  Mixed precision (FP32 /
+complex64 recurrence with FP64 reliable updates, true residual to 1e-13): 1e-8.  What
+is asserted, with tol the bar of the path:
+  * true relative errors |df| / f and ||dg|| / ||g|| at p0 (where R_s is 1-13% of S);
+  * every column of U, Z and S and every row of J_mu and J_p: relative 2-norm error;
+  * every solved column u: max |du| <= tol max |u| (pointwise field accuracy);
+  * every entry of S, J_mu, J_p, g_mu, g_p and f: |d| <= tol E, where E is the entry's
+    first-order error size under that pointwise field error (gpu_setup.oracle_scales:
+    propagation through the definitions of Sec. 3.3, no tuned floor).
+A residual stop at 1e-14 is not enough for the true relative f and g at 1e-10: S is
+a far-field functional whose relative error is 1e2-1e3 x the residual, and near the
+data f and g amplify it by ||S|| / ||R_s|| (a plain CG at 1e-14 gives 2e-10 in g on the
+32x32x16 workload, 3e-11 at 2e-15).
 """
 import numpy as np
 import pytest
@@ -19,11 +24,12 @@ from oracle import dot_oracle as orc
 from paper_1706_05586_gb300 import dot as D
 from paper_1706_05586_gb300 import synth
 from tests import problem
-from tests.gpu_setup import configure, grad_err, misfit_err, rel
+from tests.gpu_setup import (col_max_rel, col_rel, configure, entry_ratio, grad_err, misfit_err,
+                             oracle_scales, rel)
 
 pytestmark = pytest.mark.gpu
 
-FP64_RTOL = 1e-14
+FP64_RTOL = 2e-15
 
 ROB, DIR = synth.ROBIN, synth.DIRICHLET
 
@@ -110,56 +116,83 @@ def test_pals_absorption(name, ctx):
     assert np.max(np.abs(mu - pb.mu_of(pb.inp.p0))) <= 1e-12
 
 
-@pytest.mark.parametrize("name", list(CASES))
-def test_misfit_gradient_fp64(name, ctx):
+_scales = {}
+
+
+def _oracle_scales(name):
+    if name not in _scales:
+        pb, ref = _case(name)
+        _scales[name] = oracle_scales(pb, ref, pb.dmu_of(pb.inp.p0))
+    return _scales[name]
+
+
+def _check_misfit_gradient(ctx, name, prec, rtol, tol):
+    """f, g_p and S of one evaluation at p0 against the oracle, entry by entry."""
     pb, ref = _case(name)
-    configure(ctx, pb, p=pb.inp.p0, rtol=FP64_RTOL)
+    E = _oracle_scales(name)
+    configure(ctx, pb, p=pb.inp.p0, prec=prec, rtol=rtol)
     f, g, rc = D.dot_gradient(ctx, pb.wl.np_)
     assert rc == D.DOT_OK
-    assert misfit_err(f, ref) <= 1e-10
-    assert grad_err(g, ref["g_p"], ref["J_p"], ref["R_s"], ref["S"]) <= 1e-10
-    S, _ = D.dot_measurements(ctx, pb.wl.ls, pb.wl.ld, _cplx(pb))
-    assert rel(S, ref["S"]) <= 1e-10
     st = D.dot_get_stats(ctx)
-    assert st["k"] == pb.wl.ls + pb.wl.ld and st["relres_max"] <= FP64_RTOL
+    assert st["k"] == pb.wl.ls + pb.wl.ld and st["relres_max"] <= rtol
+    assert abs(f - ref["f"]) <= tol * ref["f"]
+    assert rel(g, ref["g_p"]) <= tol
+    assert abs(f - ref["f"]) <= tol * E["f"]
+    assert entry_ratio(g, ref["g_p"], E["g_p"]) <= tol
+    S, _ = D.dot_measurements(ctx, pb.wl.ls, pb.wl.ld, _cplx(pb))
+    assert col_rel(S, ref["S"]) <= tol
+    assert entry_ratio(S, ref["S"], E["S"]) <= tol
+    return st
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_misfit_gradient_fp64(name, ctx):
+    _check_misfit_gradient(ctx, name, D.PREC_FP64, FP64_RTOL, 1e-10)
+
+
+def _check_fields_jacobians(ctx, name, prec, rtol, tol):
+    pb, ref = _case(name)
+    E = _oracle_scales(name)
+    configure(ctx, pb, p=pb.inp.p0, prec=prec, rtol=rtol)
+    U, Z = D.dot_get_fields(ctx, pb.wl.n, pb.wl.ls, pb.wl.ld, _cplx(pb))
+    for X, Xr in ((U, E["U"]), (Z, E["Z"])):
+        assert col_rel(X, Xr) <= tol
+        assert col_max_rel(X, Xr) <= tol
+    Jmu, _ = D.dot_jacobian_mua(ctx, pb.wl.ls, pb.wl.ld, pb.wl.n, _cplx(pb))
+    assert col_rel(Jmu.T, ref["J_mu"].T) <= tol          # every row
+    assert entry_ratio(Jmu, ref["J_mu"], E["J_mu"]) <= tol
+    Jp, _ = D.dot_jacobian_p(ctx, pb.wl.ls, pb.wl.ld, pb.wl.np_, _cplx(pb))
+    assert col_rel(Jp.T, ref["J_p"].T) <= tol
+    assert entry_ratio(Jp, ref["J_p"], E["J_p"]) <= tol
 
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_fields_and_jacobians_fp64(name, ctx):
-    pb, ref = _case(name)
-    configure(ctx, pb, p=pb.inp.p0, rtol=FP64_RTOL)
-    U, Z = D.dot_get_fields(ctx, pb.wl.n, pb.wl.ls, pb.wl.ld, _cplx(pb))
-    assert rel(U, ref["Uf"] @ pb.inp.W) <= 1e-10
-    assert rel(Z, ref["Zf"] @ pb.inp.V) <= 1e-10
-    Jmu, _ = D.dot_jacobian_mua(ctx, pb.wl.ls, pb.wl.ld, pb.wl.n, _cplx(pb))
-    assert rel(Jmu, ref["J_mu"]) <= 1e-10
-    Jp, _ = D.dot_jacobian_p(ctx, pb.wl.ls, pb.wl.ld, pb.wl.np_, _cplx(pb))
-    assert rel(Jp, ref["J_p"]) <= 1e-10
+    _check_fields_jacobians(ctx, name, D.PREC_FP64, FP64_RTOL, 1e-10)
 
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_gradient_wrt_mua(name, ctx):
-    pb, _ = _case(name)
+    pb, ref = _case(name)
+    E = _oracle_scales(name)
     mu = pb.mu_of(pb.inp.p0)
     configure(ctx, pb, mua=mu, rtol=FP64_RTOL)
-    f, g, _ = D.dot_gradient(ctx, pb.wl.n)
-    ref = orc.evaluate(pb.D, mu, pb.grid, pb.wl.bc, pb.wl.omega_nu, pb.Bd, pb.Cd, pb.M, pb.inp.W, pb.inp.V)
-    assert grad_err(g, ref["g_mu"], ref["J_mu"], ref["R_s"], ref["S"]) <= 1e-10
+    f, g, rc = D.dot_gradient(ctx, pb.wl.n)
+    assert rc == D.DOT_OK
+    assert rel(g, ref["g_mu"]) <= 1e-10
+    assert entry_ratio(g, ref["g_mu"], E["g_mu"]) <= 1e-10
+    assert abs(f - ref["f"]) <= 1e-10 * ref["f"]
 
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_mixed_precision(name, ctx):
-    pb, ref = _case(name)
-    configure(ctx, pb, p=pb.inp.p0, prec=D.PREC_MIXED, rtol=1e-13)
-    f, g, rc = D.dot_gradient(ctx, pb.wl.np_)
-    assert rc == D.DOT_OK
-    st = D.dot_get_stats(ctx)
-    assert st["relres_max"] <= 1e-13 and st["outer_steps"] >= 2
-    assert misfit_err(f, ref) <= 1e-8
-    assert grad_err(g, ref["g_p"], ref["J_p"], ref["R_s"], ref["S"]) <= 1e-8
-    assert rel(g, ref["g_p"]) <= 1e-8
-    S, _ = D.dot_measurements(ctx, pb.wl.ls, pb.wl.ld, _cplx(pb))
-    assert rel(S, ref["S"]) <= 1e-8
+    st = _check_misfit_gradient(ctx, name, D.PREC_MIXED, 1e-13, 1e-8)
+    assert st["outer_steps"] >= 2
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_precision_fields_and_jacobians(name, ctx):
+    _check_fields_jacobians(ctx, name, D.PREC_MIXED, 1e-13, 1e-8)
 
 
 def test_gradient_at_true_parameters(ctx):
@@ -170,6 +203,11 @@ def test_gradient_at_true_parameters(ctx):
     f, g, _ = D.dot_gradient(ctx, pb.wl.np_)
     assert grad_err(g, ref["g_p"], ref["J_p"], ref["R_s"], ref["S"]) <= 1e-10
     assert misfit_err(f, ref) <= 1e-10
+    # entry by entry against each entry's first-order error size (at p_true that size
+    # is set by S, not by the noise-sized R_s)
+    E = oracle_scales(pb, ref, pb.dmu_of(pb.inp.p_true))
+    assert entry_ratio(g, ref["g_p"], E["g_p"]) <= 1e-10
+    assert abs(f - ref["f"]) <= 1e-10 * E["f"]
 
 
 # ------------------------------------------------------------------ edge cases
@@ -256,7 +294,7 @@ def test_forward_model_all_sources(name, ctx):
     # the sampled state is untouched: the next misfit uses W, V again
     f, _ = D.dot_misfit(ctx)
     out = orc.evaluate(pb.D, mu, pb.grid, pb.wl.bc, pb.wl.omega_nu, pb.Bd, pb.Cd, pb.M, pb.inp.W, pb.inp.V)
-    assert misfit_err(f, out) <= 1e-10
+    assert abs(f - out["f"]) <= 1e-10 * out["f"]
 
 
 @pytest.mark.parametrize("name", ["cplx_24x16x10_k32", "real_16x16x9_k32", "cplx_16x24x8_k48", "real_24x8x7_k16",
@@ -275,7 +313,7 @@ def test_tma_stencil_matches_direct_load_kernel(name, ctx):
     assert abs(out[1][0] - out[0][0]) <= 1e-10 * abs(out[0][0])
     assert rel(out[1][1], out[0][1]) <= 1e-9
     assert abs(out[1][2] - out[0][2]) <= 3
-    assert misfit_err(out[1][0], ref) <= 1e-8
+    assert abs(out[1][0] - ref["f"]) <= 1e-8 * ref["f"]
 
 
 @pytest.mark.parametrize("prec", [D.PREC_FP64, D.PREC_MIXED])

@@ -69,12 +69,45 @@ def test_isometric_outputs():
     assert np.allclose(V.T @ V, np.eye(2), atol=1e-12)
 
 
-def test_complex_tensor_is_real_and_imaginary_stack():
-    rng = np.random.default_rng(74)
-    J = rng.standard_normal((5, 4, 3)) + 1j * rng.standard_normal((5, 4, 3))
-    W, V, _ = orc.optimized_sources_detectors(J, 2, 2)
-    Jr = np.concatenate([J.real, J.imag], axis=2)
-    assert orc.sampled_jacobian_norm2(J, W, V) == pytest.approx(orc.sampled_jacobian_norm2(Jr, W, V), rel=1e-13)
+def test_theorem3_exact_complex_tensor():
+    """Theorem 3 for a complex Jacobian (omega != 0): when the real and the imaginary
+    slices both lie in span(A) (x) span(Bs), real isometric W, V keep all of
+    ||J||_F^2 = sum |J_ijk|^2, and steps (1)-(3) find them in one sweep."""
+    rng = np.random.default_rng(76)
+    nd, ns, npar, qd, qs = 7, 6, 5, 2, 3
+    Jr, A, Bs = _kron_rank_tensor(rng, nd, ns, npar, qd, qs)
+    Ji = np.zeros_like(Jr)
+    for _ in range(3):        # a second tensor in the same subspaces, independent of the first
+        a = A @ rng.standard_normal(qd)
+        b = Bs @ rng.standard_normal(qs)
+        Ji += np.einsum("i,j,k->ijk", a, b, rng.standard_normal(npar))
+    J = Jr + 1j * Ji
+    W, V, _ = orc.optimized_sources_detectors(J, qs, qd, maxit=1)
+    assert orc.sampled_jacobian_norm2(J, W, V) == pytest.approx(np.sum(np.abs(J) ** 2), rel=1e-12)
+    assert np.allclose(W @ W.T, Bs @ Bs.T, atol=1e-10)
+    assert np.allclose(V @ V.T, A @ A.T, atol=1e-10)
+
+
+def test_brute_force_maximum_q1_complex():
+    """q = 1 on a complex 3 x 3 x 4 tensor: the objective over real unit w, v is
+    sum_k |v^T J_k w|^2.  For a fixed v it is w^T Re(K K^H) w with K = sum_m v_m J_m, so
+    the best w is the top eigenvector of that real symmetric matrix; a dense search of v
+    over the sphere gives the global maximum, which Algorithm 1 must reach."""
+    rng = np.random.default_rng(77)
+    J = rng.standard_normal((3, 3, 4)) + 1j * rng.standard_normal((3, 3, 4))
+    W, V, _ = orc.optimized_sources_detectors(J, 1, 1, maxit=500, tol=1e-14)
+    best = 0.0
+    for th in np.linspace(0, math.pi, 181):
+        for ph in np.linspace(0, 2 * math.pi, 361):
+            v = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+            K = np.einsum("m,mjk->jk", v, J)
+            best = max(best, np.linalg.eigvalsh(np.real(K @ K.conj().T))[-1])
+    val = orc.sampled_jacobian_norm2(J, W, V)
+    # the objective at (W, V) written out as the sum over parameters of |v^T J_k w|^2
+    direct = sum(abs(V[:, 0] @ J[:, :, k] @ W[:, 0]) ** 2 for k in range(J.shape[2]))
+    assert val == pytest.approx(direct, rel=1e-12)
+    assert val >= best * (1 - 1e-9)
+    assert val <= best * (1 + 1e-3)
 
 
 def test_theorem2_complement_unbiased_enumeration():
