@@ -119,6 +119,7 @@ def test_gradient_directional_difference(setup):
             D.dot_set_pals(h, inp.p0 + s * eps * d, synth.MU_IN, synth.MU_OUT, WL.cutoff, WL.eps, WL.gamma)
             fs.append(D.dot_misfit(h)[0])
     finally:
+        D.dot_set_pals(h, inp.p0, synth.MU_IN, synth.MU_OUT, WL.cutoff, WL.eps, WL.gamma)
         D.dot_set_solver(h, D.PREC_MIXED, 1e-10, 0)
     fd = (fs[0] - fs[1]) / (2 * eps)
     gd = float(g @ d)
@@ -164,6 +165,7 @@ def test_gradient_chain_against_oracle(setup, prec):
     deterministic solve: f agrees bitwise)."""
     h, inp = setup["h"], setup["inp"]
     M = setup["M"]
+    D.dot_set_pals(h, inp.p0, synth.MU_IN, synth.MU_OUT, WL.cutoff, WL.eps, WL.gamma)
     D.dot_set_solver(h, prec, 1e-10, 0)
     try:
         f, g_p, rc = D.dot_gradient(h, WL.np_)
