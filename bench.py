@@ -309,6 +309,7 @@ def run_ours(args):
                       "parallelism": f"replicas x{ws}", "api": args.api,
                       "launch": {"graphs": True, "autotune": bool(args.autotune),
                                  "tma_stencil": last_stats["tuned_tma"] == 1,
+                                 "direction_fused_into_stencil": last_stats["fused_direction"] == 1,
                                  "blocks_per_sm": last_stats["tuned_blocks_per_sm"]}},
            "clocks": clk, "gpu_launches": int(launches), "roofline": roofline}
 
@@ -319,11 +320,11 @@ def run_ours(args):
         p_last = p_dev[args.warmup + args.steps - 1]
         cplx = wl.omega_nu != 0.0
 
-        def timed_eval(prec, rtol, reps=1):
+        def timed_eval(prec, rtol, reps=1, maxit=0):
             """Whole evaluations at the last p, each from scratch (p set again: PaLS,
             coefficients, right-hand sides, solve and post-processing all rerun); mean
             CUDA-event time per evaluation and the last one's outputs."""
-            D.dot_set_solver(ctx, prec, rtol, 0)
+            D.dot_set_solver(ctx, prec, rtol, maxit)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(reps):
@@ -338,19 +339,22 @@ def run_ours(args):
 
         rel = lambda a, b: float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
         S_last, _ = D.dot_measurements(ctx, wl.ls, wl.ld, cplx)
-        ref = timed_eval(D.PREC_FP64, 1e-14)
-        ref_rtol = 1e-14
+        # the tightest FP64 stopping rule the true residual resolves on this grid: 3e-14 if
+        # it converges within 3x the iterations of the benchmark's rule, else 1e-13
+        fa = timed_eval(D.PREC_FP64, args.rtol)
+        ref, ref_rtol = timed_eval(D.PREC_FP64, 3e-14, maxit=3 * fa["iters"]), 3e-14
         if not ref["converged"]:
             ref, ref_rtol = timed_eval(D.PREC_FP64, 1e-13), 1e-13
 
         def errs(x):
             return {"f": abs(x["f"] - ref["f"]) / abs(ref["f"]), "g": rel(x["g"], ref["g"]), "S": rel(x["S"], ref["S"])}
 
-        fa = timed_eval(D.PREC_FP64, args.rtol)
         out["fp64_path"] = {"evals_per_s": round(1e3 / fa["ms"], 4), "ms_per_eval": round(fa["ms"], 1),
                             "rtol": args.rtol, "iters": fa["iters"],
                             "speedup_of_mixed": round(fa["ms"] / (ms_max / args.steps), 3)}
-        out["err_vs_fp64"] = {"reference": "plain FP64 GPU path at rtol %.0e (%d iterations)" % (ref_rtol, ref["iters"]),
+        out["err_vs_fp64"] = {"reference": "plain FP64 GPU path at rtol %.0e (%d iterations; the tightest "
+                                           "stopping rule its FP64 true residual resolves here)"
+                                           % (ref_rtol, ref["iters"]),
                               "mixed": {"f": abs(f_last - ref["f"]) / abs(ref["f"]), "g": rel(g_last, ref["g"]),
                                         "S": rel(S_last, ref["S"])},
                               "fp64_same_rtol": errs(fa)}

@@ -81,6 +81,9 @@ typedef struct dot_stats {
     int64_t kernel_launches; /* cumulative number of this library's kernel launches   */
     int32_t tuned_tma;       /* stencil path of the last solve, autotuned or default (1 TMA, 0 direct, -1 no solve yet) */
     int32_t tuned_blocks_per_sm; /* blocks per SM of the vector kernels in the last solve (-1 no solve yet) */
+    int32_t fused_direction; /* 1: the last solve ran the direction update inside the TMA stencil, 0: as a
+                                pass of its own (-1 no solve yet)                                       */
+    int32_t reserved;        /* 0                                                                  */
 } dot_stats;
 
 /* Per-kernel device time of the Krylov kernels, accumulated while timing is on.
@@ -236,11 +239,16 @@ int dot_set_direction_ring(dot_ctx* ctx, int slots);
  * per-context semantics and outputs as dot_gradient (f[i], g[i]); each context must
  * appear once. */
 int dot_gradient_batch(dot_ctx* const* ctxs, int count, double* f, double* const* g);
-/* Stencil implementation of the block solve: tma != 0 (default) stages p through
- * shared memory with tensor-memory-accelerator copies wherever the block allows it
- * (FP32/complex64 recurrence, nx and ny multiples of 8, padded block width a
- * multiple of 32); 0 always uses the direct-load kernel.  Results agree to rounding. */
-int dot_set_stencil_path(dot_ctx* ctx, int tma);
+/* Stencil implementation of the block solve (no counterpart in the paper, which leaves
+ * the solver open).  mode 2 (default): wherever the block allows it (FP32/complex64
+ * recurrence, nx and ny multiples of 8, padded block width a multiple of 32 real or 16
+ * complex columns) one kernel forms the new search direction p = M^{-1} r~ + beta p and
+ * applies the stencil to it, staging r~, the old direction and the coefficients
+ * through shared memory with tensor-memory-accelerator copies; mode 1: the
+ * TMA-staged stencil after a separate direction pass (block width a multiple of 16);
+ * mode 0: the direct-load stencil.  Shapes a mode does not take fall back to the next
+ * lower one.  Results agree to rounding.  Errors: DOT_EINVAL for other modes. */
+int dot_set_stencil_path(dot_ctx* ctx, int mode);
 /* Kernel timing: enable != 0 resets the counters and records CUDA events around
  * every Krylov kernel launch (on the context stream); 0 stops recording. */
 int dot_set_kernel_timing(dot_ctx* ctx, int enable);

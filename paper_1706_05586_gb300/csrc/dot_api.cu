@@ -11,12 +11,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dot.h"
 #include "dot_internal.h"
 
 using namespace dotk;
 
 namespace {
+
+// NVTX range over one phase of an evaluation (host side; a profiler shows it over the
+// kernels the phase queues).  Costs a function call when no tool is attached.
+struct Phase {
+    explicit Phase(const char* name) { nvtxRangePushA(name); }
+    ~Phase() { nvtxRangePop(); }
+    Phase(const Phase&) = delete;
+    Phase& operator=(const Phase&) = delete;
+};
 
 thread_local std::string g_err;
 
@@ -100,6 +111,7 @@ struct SolveRun {
     DirRing ring;
     TmaStencil tma;
     bool tma_ready = false;
+    bool fused = false;  // the direction update runs inside the TMA stencil
     OpRaw oi{}, o64{};
     double delta = 0.0;
     int maxit = 0;
@@ -163,6 +175,7 @@ struct dot_ctx {
 
     bool coef_valid = false;
     DevBuf cf64, dinv64, cf32, dinv32;  // packed (cx, cy, cz, dre) and Jacobi inverse diagonal
+    DevBuf cf8;                         // 32-byte FP32 records (coefficients + Jacobi inverse)
 
     int ns = 0, nd = 0;
     DevBuf rpB, ciB, vB, rpC, ciC, vC, cpC, rwC, vCc;
@@ -178,7 +191,7 @@ struct dot_ctx {
     double rtol = 1e-10;
     int maxit = 0;
     double delta = 1e-3;  // reliable-update threshold of the mixed-precision recurrence
-    bool use_tma = true;  // TMA-staged stencil where the block shape allows it
+    int stencil_mode = 2;  // 2: TMA stencil with the direction update fused, 1: TMA stencil, 0: direct loads
 
     // block vectors: FP64 right-hand side, solution and true residual; the recurrence
     // vectors x~, r~, p, q in the inner precision
@@ -200,6 +213,7 @@ struct dot_ctx {
     bool autotune = false;
     TunedChoice tuned;
     Tuning last_cfg{false, -1};  // launch configuration of the last solve (blocks_per_sm -1: none yet)
+    bool last_fused = false;     // the last solve ran the direction update inside the stencil
     int ring_cap = kDirRingMax;  // most direction-ring slots to try (dot_set_direction_ring)
     cudaEvent_t bev[2] = {nullptr, nullptr};
 
@@ -271,6 +285,7 @@ OpRaw op32(const dot_ctx* c) {
 // ------------------------------------------------------------------ stages
 int ensure_coefficients(dot_ctx* c) {
     if (c->coef_valid) return DOT_OK;
+    Phase ph("dot: PaLS absorption and operator coefficients");
     if (!c->D_set) return fail(DOT_ESTATE, "dot_set_diffusion has not been called");
     if (c->mu_mode == 0) return fail(DOT_ESTATE, "neither dot_set_mua nor dot_set_pals has been called");
     const int64_t n = c->n;
@@ -285,8 +300,9 @@ int ensure_coefficients(dot_ctx* c) {
     TRY(ensure(c->cf32, n * 16));
     TRY(ensure(c->dinv64, n * 16));
     TRY(ensure(c->dinv32, n * 8));
+    TRY(ensure(c->cf8, n * 32));
     CK(build_coefficients(c->D.as<double>(), c->mu.as<double>(), c->nx, c->ny, c->nz, c->h, c->bc, c->w, c->cf64.p,
-                          c->dinv64.p, cplx(c), c->cf32.p, c->dinv32.p, c->s));
+                          c->dinv64.p, cplx(c), c->cf32.p, c->dinv32.p, c->cf8.p, c->s));
     count(c, c->mu_mode == 2 ? 2 : 1);
     c->coef_valid = true;
     return DOT_OK;
@@ -351,10 +367,10 @@ int read_counts(dot_ctx* c, const ColState& st, int* act, int* upd) {
 
 constexpr int kPoll = 8;  // iterations between host polls
 
-int collect_step_timing(dot_ctx* c, int steps, bool first_without_p, int H) {
+int collect_step_timing(dot_ctx* c, int steps, bool first_without_p, int H, bool fused) {
     for (int m = 0; m < steps; ++m) {
         float ms = 0.f;
-        if (!(first_without_p && m == 0)) {
+        if (!(first_without_p && m == 0) && !fused) {
             CK(cudaEventElapsedTime(&ms, c->tev[4 * m], c->tev[4 * m + 1]));
             c->kt.ms[2] += ms;
             c->kt.launches[2] += 1;
@@ -394,8 +410,12 @@ int apply_tuning(dot_ctx* c, SolveRun& r, const Tuning& t) {
     r.ring.flush_grid = (int)std::max<int64_t>(1, std::min(need, gf));
     if (t.tma && !r.tma_ready) {
         CK(tma_stencil_prepare(r.inner, r.ring, c->cf32.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma));
+        r.tma.fused = false;
+        if (c->stencil_mode == 2 && dpq_eligible(r.inner, c->nx, c->ny, r.kp))
+            CK(dpq_prepare(r.inner, r.ring, c->ri.p, c->cf8.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma));
         r.tma_ready = true;
     }
+    r.fused = t.tma && r.tma.fused;
     run_release_graph(r);
     r.graph_failed = false;
     return DOT_OK;
@@ -435,7 +455,7 @@ int solve_begin(dot_ctx* c, int kp, int kr) {
     r.delta = r.mixed ? c->delta : 0.0;
     r.maxit = c->maxit > 0 ? c->maxit : 10 * (c->nx + c->ny + c->nz);
     const bool tma_ok = tma_stencil_eligible(r.inner, c->nx, c->ny, kp);
-    Tuning base{c->use_tma && tma_ok, 5};  // five 256-thread blocks per SM: one wave at the update kernel's register limit
+    Tuning base{c->stencil_mode != 0 && tma_ok, 5};  // five 256-thread blocks per SM: one wave at the update kernel's register limit
     if (c->autotune) {
         const bool have = c->tuned.valid && c->tuned.n == r.n && c->tuned.kp == kp && c->tuned.inner == (int)r.inner;
         if (have) {
@@ -473,6 +493,7 @@ int launch_batch(dot_ctx* c, SolveRun& r, bool first_batch) {
 int solve_advance(dot_ctx* c) {
     SolveRun& r = c->run;
     if (r.done) return DOT_OK;
+    Phase ph("dot: Krylov iterations");
     const bool first_batch = r.first;
     const bool tuning = r.cand_at >= 0;
     r.batch_timed = tuning;
@@ -505,7 +526,9 @@ int solve_advance(dot_ctx* c) {
     } else {
         TRY(launch_batch(c, r, first_batch));
     }
-    count(c, kPoll * 3 - (first_batch ? 1 : 0) + kPoll / r.ring.H);  // plus the ring flushes
+    // direction, stencil and update per iteration (the first of a solve has no direction;
+    // fused: stencil with direction and update), plus the ring flushes
+    count(c, (r.fused ? kPoll * 2 : kPoll * 3 - (first_batch ? 1 : 0)) + kPoll / r.ring.H);
     if (tuning) CK(cudaEventRecord(c->bev[1], c->s));
     r.first = false;
     r.it += kPoll;
@@ -518,7 +541,7 @@ int solve_poll(dot_ctx* c) {
     if (r.done) return DOT_OK;
     const bool first_batch = r.it == kPoll;
     TRY(read_counts(c, r.st, &r.act, &r.upd));
-    if (c->timing) TRY(collect_step_timing(c, kPoll, first_batch, r.ring.H));
+    if (c->timing) TRY(collect_step_timing(c, kPoll, first_batch, r.ring.H, r.fused));
     if (r.batch_timed) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->bev[0], c->bev[1]));
@@ -545,6 +568,7 @@ int solve_poll(dot_ctx* c) {
         r.batch_timed = false;
     }
     if (r.upd > 0) {
+        Phase ph("dot: reliable update (FP64 true residual)");
         if (c->timing) CK(cudaEventRecord(c->tev[32], c->s));
         CK(solve_refresh(r.inner, r.oi, r.o64, c->b64.p, c->x64.p, c->r64.p, c->xi.p, c->ri.p, r.n, r.kp, r.st,
                          c->rtol, r.maxit, r.L, c->num_sms, c->s));
@@ -569,6 +593,7 @@ int solve_end(dot_ctx* c) {
     SolveRun& r = c->run;
     const int kp = r.kp;
     c->last_cfg = r.cfg;
+    c->last_fused = r.fused;
     std::vector<int> iters(kp), updates(kp), status(kp), active(kp);
     std::vector<double> rr(kp), bb(kp);
     CK(cudaMemcpyAsync(status.data(), r.st.status, kp * 4, cudaMemcpyDeviceToHost, c->s));
@@ -601,9 +626,18 @@ int solve_end(dot_ctx* c) {
             itmax = std::max(itmax, iters[j]);
         }
         const double nn = (double)r.n, rs = r.mixed ? 4.0 : 8.0;
-        c->kt.bytes[0] += ci * nn * 2.0 * r.ei + itmax * nn * 4.0 * rs;
+        if (r.fused) {
+            // fused launches read r~ and the old direction and write the new direction and
+            // q (4 vectors) and one 32-byte record per cell; the first iteration of the
+            // solve is a plain stencil (p and q, 16 bytes of coefficients per cell)
+            double first = 0.0;
+            for (int j = 0; j < kp; ++j) first += iters[j] > 0 ? 1.0 : 0.0;
+            c->kt.bytes[0] += (ci - first) * nn * 4.0 * r.ei + first * nn * 2.0 * r.ei + itmax * nn * 32.0;
+        } else {
+            c->kt.bytes[0] += ci * nn * 2.0 * r.ei + itmax * nn * 4.0 * rs;
+            c->kt.bytes[2] += ci * nn * 3.0 * r.ei + itmax * nn * r.ei;
+        }
         c->kt.bytes[1] += ci * nn * 3.0 * r.ei + itmax * nn * r.ei;
-        c->kt.bytes[2] += ci * nn * 3.0 * r.ei + itmax * nn * r.ei;
         c->kt.bytes[4] += ci * nn * r.ei + ci / r.ring.H * nn * 2.0 * r.ei;
     }
     float ms_solve = 0;
@@ -643,6 +677,7 @@ int solve_end(dot_ctx* c) {
 int fields_begin(dot_ctx* c) {
     c->run.active = false;
     if (c->fields_valid) return DOT_OK;
+    Phase ph("dot: right-hand sides and solve start");
     TRY(ensure_coefficients(c));
     if (c->ns == 0) return fail(DOT_ESTATE, "dot_set_sources has not been called");
     if (c->nd == 0) return fail(DOT_ESTATE, "dot_set_detectors has not been called");
@@ -699,6 +734,7 @@ int ensure_projection(dot_ctx* c) {
 int ensure_post(dot_ctx* c) {
     TRY(ensure_fields(c));
     if (c->post_valid) return DOT_OK;
+    Phase ph("dot: restriction and misfit");
     if (c->M_set) TRY(ensure_projection(c));
     const size_t nr = (size_t)std::max(c->ls, 1) * std::max(c->ld, 1);
     TRY(ensure(c->Tm, (size_t)c->nd * std::max(c->ls, 1) * 16));
@@ -805,7 +841,7 @@ int dot_destroy(dot_ctx* c) {
     if (!c) return DOT_OK;
     cudaSetDevice(c->device);
     if (c->s) cudaStreamSynchronize(c->s);
-    DevBuf* bufs[] = {&c->D, &c->mu, &c->phi, &c->wdmu, &c->p, &c->cf64, &c->dinv64, &c->cf32, &c->dinv32, &c->rpB, &c->ciB, &c->vB, &c->rpC,
+    DevBuf* bufs[] = {&c->D, &c->mu, &c->phi, &c->wdmu, &c->p, &c->cf64, &c->dinv64, &c->cf32, &c->dinv32, &c->cf8, &c->rpB, &c->ciB, &c->vB, &c->rpC,
                       &c->ciC, &c->vC, &c->cpC, &c->rwC, &c->vCc, &c->W, &c->V, &c->M, &c->MW, &c->P, &c->b64,
                       &c->x64, &c->r64, &c->xi, &c->ri, &c->pi, &c->qi, &c->colbuf, &c->partA, &c->partB, &c->gcount, &c->Tm,
                       &c->S, &c->Rs, &c->f, &c->gmu, &c->gp, &c->J, &c->tmp};
@@ -1027,6 +1063,7 @@ int gradient_impl(dot_ctx* c, double* f, double* g, cudaMemcpyKind kind) {
     if (!f || !g) return fail(DOT_EINVAL, "null output");
     if (!c->M_set) return fail(DOT_ESTATE, "dot_set_data has not been called");
     TRY(ensure_post(c));
+    Phase ph("dot: sensitivity and PaLS chain rule");
     CK(cudaEventRecord(c->ev[3], c->s));
     TRY(ensure(c->gmu, c->n * 8));
     CK(sensitivity_gmu(cplx(c), c->x64.p, c->n, c->kp, c->ls, c->ld, c->Rs.as<double>(), c->gmu.as<double>(), c->s));
@@ -1254,6 +1291,7 @@ int dot_get_stats(dot_ctx* c, dot_stats* out) {
     *out = c->stats;
     out->tuned_tma = c->last_cfg.blocks_per_sm < 0 ? -1 : (c->last_cfg.tma ? 1 : 0);
     out->tuned_blocks_per_sm = c->last_cfg.blocks_per_sm;
+    out->fused_direction = c->last_cfg.blocks_per_sm < 0 ? -1 : (c->last_fused ? 1 : 0);
     return DOT_OK;
 }
 
@@ -1317,9 +1355,10 @@ int dot_gradient_batch(dot_ctx* const* ctxs, int count, double* f, double* const
     return DOT_OK;
 }
 
-int dot_set_stencil_path(dot_ctx* c, int tma) {
+int dot_set_stencil_path(dot_ctx* c, int mode) {
     TRY(need_ctx(c));
-    c->use_tma = tma != 0;
+    if (mode < 0 || mode > 2) return fail(DOT_EINVAL, "stencil path must be 0, 1 or 2");
+    c->stencil_mode = mode;
     invalidate_fields(c);
     return DOT_OK;
 }

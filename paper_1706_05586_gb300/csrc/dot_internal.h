@@ -85,6 +85,14 @@ struct TmaStencil {
     int zc = 0;                           // z planes per work item
     int grid = 0;
     size_t smem = 0;
+    // direction update fused into the stencil (k_dpq_tma): maps over r~ and the ring
+    // slots with kcf-column boxes, and over the 32-byte coefficient records
+    alignas(64) unsigned char tmap_r[128];
+    alignas(64) unsigned char tmap_pf[kDirRingMax][128];
+    alignas(64) unsigned char tmap_c8[128];
+    bool fused = false;
+    int kcf = 0, zcf = 0, gridf = 0;
+    size_t smemf = 0;
 };
 bool tma_stencil_eligible(ElemKind inner, int nx, int ny, int kp);
 // Launch the bounded-wait self-test: *err (device) becomes 1 when the wait gave up.
@@ -95,6 +103,15 @@ cudaError_t tma_stencil_prepare(ElemKind inner, const DirRing& ring, const void*
 // step-length history).
 cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& op, const TmaStencil& t, int slot, void* q, int kp,
                                const ColState& st, cudaStream_t s);
+// Direction update fused into the stencil: p_new = M^{-1} r~ + beta p_old into ring slot
+// `slot` from slot `prev` (running columns; p_old carried over on the others), then
+// q = A p_new with p_new^T q.  Eligible for the FP32 / complex64 recurrence with nx, ny
+// multiples of 8 and the padded block width a multiple of 32 (real) or 16 (complex).
+bool dpq_eligible(ElemKind inner, int nx, int ny, int kp);
+cudaError_t dpq_prepare(ElemKind inner, const DirRing& ring, const void* r, const void* cf8, int nx, int ny, int nz,
+                        int kp, int num_sms, TmaStencil* out);
+cudaError_t dpq_launch(ElemKind inner, const OpRaw& op, const TmaStencil& t, const DirRing& ring, int slot, int prev,
+                       void* q, int kp, const ColState& st, cudaStream_t s);
 
 // Launch shape of the scalar kernels (one column per thread, four blocks per SM).
 Launch krylov_launch(int64_t n, int kp, int num_sms);
@@ -109,7 +126,8 @@ int vector_width(ElemKind inner);
 cudaError_t solve_start(ElemKind inner, const OpRaw& op, const void* b64, void* x64, void* x, void* r, void* p,
                         int64_t n, int kp, const ColState& st, double rtol, const Launch& L, cudaStream_t s);
 // Krylov iteration m of a batch (the batch starts at a multiple of the ring size):
-// [direction update into slot m mod H,] stencil q = A p with p^T q, r~ update with
+// [direction update into slot m mod H (fused into the stencil when tma->fused),]
+// stencil q = A p with p^T q, r~ update with
 // convergence / refresh decisions, and, when slot m mod H is the ring's last, the
 // flush x~ += sum_j alpha_j p_j.  ev, when not null, receives four event records
 // around the first three launches; evf, when not null, one record after the flush.
@@ -132,10 +150,12 @@ cudaError_t pals_eval(const double* p, int m0, double mu_in, double mu_out, doub
                       double gamma, int nx, int ny, int nz, double h, double* phi, double* mu,
                       double* wdmu, cudaStream_t s);
 // Packed coefficients (cx, cy, cz, dre) per voxel in FP64 (cf64) and FP32 (cf32),
-// and the Jacobi inverse diagonal in both precisions.
+// and the Jacobi inverse diagonal in both precisions; cf8 (optional, 32 B per voxel):
+// the FP32 coefficients followed by the FP32 Jacobi inverse (re, im or value, 0) and
+// two zero words, the record the fused direction + stencil kernel stages by TMA.
 cudaError_t build_coefficients(const double* D, const double* mu, int nx, int ny, int nz, double h,
                                const int bc[6], double w, void* cf64, void* dinv64, bool cplx, void* cf32,
-                               void* dinv32, cudaStream_t s);
+                               void* dinv32, void* cf8, cudaStream_t s);
 cudaError_t build_rhs(bool cplx, const int64_t* rowptrB, const int32_t* colB, const double* valB,
                       const double* W, int ns, int ls, const int64_t* rowptrC, const int32_t* colC,
                       const double* valC, const double* V, int nd, int ld, int64_t n, int kp, void* X,

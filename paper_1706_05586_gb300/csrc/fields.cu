@@ -159,7 +159,7 @@ struct Bc6 { int f[6]; };
 
 __global__ void k_coefficients(const double* __restrict__ D, const double* __restrict__ mu, int nx, int ny, int nz,
                                double h, Bc6 bc, double w, Cf4<double>* __restrict__ cf64, double* dinv64, int cplx,
-                               Cf4<float>* __restrict__ cf32, float* dinv32) {
+                               Cf4<float>* __restrict__ cf32, float* dinv32, float4* __restrict__ cf8) {
     const int64_t n = (int64_t)nx * ny * nz;
     const int64_t nxy = (int64_t)nx * ny;
     const double h2 = h * h;
@@ -188,27 +188,36 @@ __global__ void k_coefficients(const double* __restrict__ D, const double* __res
         c32.cz = (float)fzp;
         c32.dre = (float)d;
         cf32[v] = c32;
+        float2 di;
         if (cplx) {
             // 1 / (d + i w) = (d - i w) / (d^2 + w^2)
             const double den = d * d + w * w;
             const double re = d / den, im = -w / den;
             reinterpret_cast<double2*>(dinv64)[v] = make_double2(re, im);
-            reinterpret_cast<float2*>(dinv32)[v] = make_float2((float)re, (float)im);
+            di = make_float2((float)re, (float)im);
+            reinterpret_cast<float2*>(dinv32)[v] = di;
         } else {
             dinv64[v] = 1.0 / d;
-            dinv32[v] = (float)(1.0 / d);
+            di = make_float2((float)(1.0 / d), 0.f);
+            dinv32[v] = di.x;
+        }
+        // 32-byte record of the fused direction + stencil kernel: the four coefficients
+        // and the FP32 Jacobi inverse, bitwise the values of cf32 and dinv32
+        if (cf8) {
+            cf8[2 * v] = make_float4(c32.cx, c32.cy, c32.cz, c32.dre);
+            cf8[2 * v + 1] = make_float4(di.x, di.y, 0.f, 0.f);
         }
     }
 }
 
 cudaError_t build_coefficients(const double* D, const double* mu, int nx, int ny, int nz, double h, const int bc[6],
-                               double w, void* cf64, void* dinv64, bool cplx, void* cf32, void* dinv32,
+                               double w, void* cf64, void* dinv64, bool cplx, void* cf32, void* dinv32, void* cf8,
                                cudaStream_t s) {
     Bc6 b;
     for (int f = 0; f < 6; ++f) b.f[f] = bc[f];
     const int64_t n = (int64_t)nx * ny * nz;
     k_coefficients<<<grid_for(n, 256), 256, 0, s>>>(D, mu, nx, ny, nz, h, b, w, (Cf4<double>*)cf64, (double*)dinv64,
-                                                    cplx ? 1 : 0, (Cf4<float>*)cf32, (float*)dinv32);
+                                                    cplx ? 1 : 0, (Cf4<float>*)cf32, (float*)dinv32, (float4*)cf8);
     return cudaGetLastError();
 }
 

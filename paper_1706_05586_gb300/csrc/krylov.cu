@@ -664,15 +664,21 @@ cudaError_t kry_step(ElemKind inner, const OpRaw& o, void* x, void* r, const Dir
         // blocks wider than 256 threads (one column per thread at block widths above
         // 256 x the vector width) take the instantiations compiled for 1024 threads
         const bool wide = Lv.threads > 256;
+        // the direction update fused into the TMA stencil: one launch streams r~ and the
+        // old direction in and the new direction and q out
+        const bool fused = with_p && tma && tma->fused;
         if (ev) record_timing(ev[0], s);
-        if (with_p) {
+        if (with_p && !fused) {
             if (wide)
                 k_dir<T, 1024><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, p_old, p_new, n, kp, Lv.slots, st);
             else
                 k_dir<T, 256><<<Lv.grid, Lv.threads, 0, s>>>(op, (const T*)r, p_old, p_new, n, kp, Lv.slots, st);
         }
         if (ev) record_timing(ev[1], s);
-        if (tma) {
+        if (fused) {
+            const cudaError_t e = dpq_launch(inner, o, *tma, ring, slot, prev, q, kp, st, s);
+            if (e != cudaSuccess) return e;
+        } else if (tma) {
             const cudaError_t e = tma_stencil_launch(inner, o, *tma, slot, q, kp, st, s);
             if (e != cudaSuccess) return e;
         } else if (wide) {

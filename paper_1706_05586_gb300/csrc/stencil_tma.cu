@@ -294,6 +294,220 @@ __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __gr
     }
 }
 
+// ------------------------------------------------------------------------------
+// Direction update fused into the stencil.  One pass computes, for the direction of
+// iteration m,
+//     p_new = M^{-1} r~ + beta p_old   (running columns; p_old carried over otherwise)
+//     q = A p_new,  p_new^T q
+// writing p_new into its ring slot and q, so the iteration streams r~ and p_old in and
+// p_new and q out (4 block vectors) instead of the 3 + 2 of a direction pass followed
+// by the stencil.  Each plane of the tile arrives with its one-cell halo by three
+// cp.async.bulk.tensor loads on one mbarrier: r~ and p_old into one of S staging slots
+// and the 32-byte records (coefficients, FP32 Jacobi inverse) into a ring of S + 3
+// coefficient planes.  The plane is then converted once, halo included, into a ring
+// of three p_new planes (k-1, k, k+1) that the stencil reads; out-of-grid cells arrive
+// as zeros in r~, p_old and M^{-1}, so their p_new is an exact zero as well.  The
+// staging slot is refilled as soon as its plane is converted, so S planes are in
+// flight while a plane is computed.  A lane owns one column (KC = 16 complex or 32
+// real columns: 128-byte rows).
+template <typename T, int KC, int S>
+struct DpqLayout {
+    static constexpr int PLANE = KC * HX * HY;                 // elements of one vector plane
+    static constexpr int P_BYTES = PLANE * (int)sizeof(T);
+    static constexpr int C8_BYTES = HX * HY * 32;              // one plane of 32-byte records
+    static constexpr int C8_SLOT = (C8_BYTES + 127) / 128 * 128;
+    static constexpr int NCF = S + 3;                          // coefficient planes alive
+    static constexpr int OFF_PN = 0;                           // 3 converted planes
+    static constexpr int OFF_ST = OFF_PN + 3 * P_BYTES;        // S x (r~ plane, p_old plane)
+    static constexpr int OFF_CF = OFF_ST + S * 2 * P_BYTES;    // NCF coefficient planes
+    static constexpr int OFF_BAR = OFF_CF + NCF * C8_SLOT;     // S mbarriers
+    static constexpr int OFF_ACC = OFF_BAR + (S * 8 + 15) / 16 * 16;  // kp column accumulators
+    static_assert(P_BYTES % 128 == 0 && C8_SLOT % 128 == 0, "TMA destinations on 128-byte boundaries");
+    static_assert(TY * 32 * (int)sizeof(double2) <= 2 * P_BYTES, "per-warp partials fit in staging slot 0");
+};
+
+__device__ __forceinline__ float dinv_of(float4 w, float*) { return w.x; }
+__device__ __forceinline__ float2 dinv_of(float4 w, float2*) { return make_float2(w.x, w.y); }
+
+template <typename T, int KC, int S>
+__global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ CUtensorMap tr,
+                                                        const __grid_constant__ CUtensorMap tp,
+                                                        const __grid_constant__ CUtensorMap tc8, Op<T> op,
+                                                        T* __restrict__ p_new, T* __restrict__ q, int kp,
+                                                        int zc_len, ColState st, int hslot) {
+    using Ly = DpqLayout<T, KC, S>;
+    constexpr int LPC = KC;           // lanes per cell, one column each
+    constexpr int XS = 32 / LPC;      // cells per warp instruction
+    static_assert(LPC == 16 || LPC == 32, "column tile");
+    constexpr int PLANE = Ly::PLANE;
+    constexpr int P_BYTES = Ly::P_BYTES;
+    unsigned char* base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    T* pn_ring = reinterpret_cast<T*>(base + Ly::OFF_PN);
+    unsigned char* stg = base + Ly::OFF_ST;
+    unsigned char* cfr = base + Ly::OFF_CF;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + Ly::OFF_BAR);
+    double2* acc = reinterpret_cast<double2*>(base + Ly::OFF_ACC);
+    double2* wsum = reinterpret_cast<double2*>(stg);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = lane % LPC, xsub = lane / LPC;
+    const int nx = op.nx, ny = op.ny, nz = op.nz;
+    const int tiles_x = nx / TX, tiles_y = ny / TY, tiles_c = kp / KC;
+    const int zchunks = (nz + zc_len - 1) / zc_len;
+    const int nitems = tiles_x * tiles_y * tiles_c * zchunks;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < S; ++b) mbar_init(&bar[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int c = threadIdx.x; c < kp; c += blockDim.x) acc[c] = make_double2(0.0, 0.0);
+    __syncthreads();
+
+    uint32_t parity = 0;    // bit b: parity of the next phase of staging slot b
+    uint32_t pending = 0;   // bit b: a copy into staging slot b has been issued and not waited for
+    bool failed = false;
+
+    for (int item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
+        int rem = item;
+        const int txi = rem % tiles_x;
+        rem /= tiles_x;
+        const int tyi = rem % tiles_y;
+        rem /= tiles_y;
+        const int cci = rem % tiles_c;
+        const int zci = rem / tiles_c;
+        const int i0 = txi * TX, j0 = tyi * TY, c0 = cci * KC;
+        const int z0 = zci * zc_len, z1 = min(z0 + zc_len, nz);
+        const int cu = c0 + col;
+        const bool act = st.active[cu] != 0;
+        const bool run = act && !st.upd[cu];
+        // a tile whose columns have all stopped needs neither p_new nor q
+        if (!__syncthreads_or(act)) continue;
+        const T bt = run ? enarrow<T>(st.beta[cu]) : ezero<T>();
+
+        // planes z0-1 .. z1 (z1 is the halo below the chunk; zero-filled past the grid)
+        auto sslot = [&](int z) { return (z - z0 + 1) % S; };
+        auto pslot = [&](int z) { return (z - z0 + 1) % 3; };
+        auto cslot = [&](int z) { return (z - z0 + 1) % Ly::NCF; };
+        auto issue = [&](int z) {
+            const int sl = sslot(z);
+            unsigned char* d = stg + (size_t)sl * 2 * P_BYTES;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar[sl], 2 * P_BYTES + Ly::C8_BYTES);
+            tma_load4(&tr, d, &bar[sl], c0, i0 - 1, j0 - 1, z);
+            tma_load4(&tp, d + P_BYTES, &bar[sl], c0, i0 - 1, j0 - 1, z);
+            tma_load4(&tc8, cfr + (size_t)cslot(z) * Ly::C8_SLOT, &bar[sl], 0, i0 - 1, j0 - 1, z);
+        };
+        // (the barrier above also ends the previous item's reads of the partials in slot 0)
+        for (int z = z0 - 1; z <= min(z0 - 2 + S, z1); ++z) {
+            if (threadIdx.x == 0) issue(z);
+            pending |= 1u << sslot(z);
+        }
+        // wait for plane z, convert it into its p_new slot (and, for the chunk's own
+        // planes, write the tile's cells to the ring slot in global memory), then hand
+        // the staging slot to plane z + S
+        auto convert = [&](int z) -> bool {
+            const int sl = sslot(z);
+            const bool ok = mbar_wait(&bar[sl], (parity >> sl) & 1u);
+            if (ok) {
+                parity ^= 1u << sl;
+                pending &= ~(1u << sl);
+            }
+            if (__syncthreads_or(!ok)) return false;
+            const T* Rr = reinterpret_cast<const T*>(stg + (size_t)sl * 2 * P_BYTES);
+            const T* Po = reinterpret_cast<const T*>(stg + (size_t)sl * 2 * P_BYTES + P_BYTES);
+            const float4* cw = reinterpret_cast<const float4*>(cfr + (size_t)cslot(z) * Ly::C8_SLOT);
+            T* Pn = pn_ring + pslot(z) * PLANE;
+            const bool own = z >= z0 && z < z1;
+            for (int cell = warp * XS + xsub; cell < HX * HY; cell += TY * XS) {
+                const int o = cell * LPC + col;
+                const T po = Po[o];
+                T pn = po;
+                if (run) pn = eadd(emul(dinv_of(cw[2 * cell + 1], (T*)nullptr), Rr[o]), emul(bt, po));
+                Pn[o] = pn;
+                const int hy = cell / HX, hx = cell - hy * HX;
+                if (own && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
+                    const int64_t v = (int64_t)(i0 + hx - 1) + (int64_t)nx * ((j0 + hy - 1) + (int64_t)ny * z);
+                    p_new[v * kp + cu] = pn;
+                }
+            }
+            __syncthreads();  // staging slot read, p_new plane written
+            if (z + S <= z1) {
+                if (threadIdx.x == 0) issue(z + S);
+                pending |= 1u << sslot(z + S);
+            }
+            return true;
+        };
+        failed = !convert(z0 - 1) || !convert(z0);
+        T pq = ezero<T>();
+        for (int k = z0; k < z1 && !failed; ++k) {
+            if (!convert(k + 1)) {
+                failed = true;
+                break;
+            }
+            const T* pm = pn_ring + pslot(k - 1) * PLANE;
+            const T* pc = pn_ring + pslot(k) * PLANE;
+            const T* pn = pn_ring + pslot(k + 1) * PLANE;
+            const float4* cm = reinterpret_cast<const float4*>(cfr + (size_t)cslot(k - 1) * Ly::C8_SLOT);
+            const float4* cc = reinterpret_cast<const float4*>(cfr + (size_t)cslot(k) * Ly::C8_SLOT);
+            const int j = j0 + warp;
+            const int row = (warp + 1) * HX * LPC;
+            const int crow = (warp + 1) * HX;
+#pragma unroll 2
+            for (int xi = xsub; xi < TX; xi += XS) {
+                const int i = i0 + xi;
+                const int v = i + nx * (j + ny * k);
+                const int o = row + (xi + 1) * LPC + col;
+                const int co = crow + xi + 1;
+                const float4 cv = cc[2 * co];   // (cx, cy, cz, dre)
+                const T xc = pc[o];
+                T a = escale(cv.w, xc);
+                if constexpr (Elem<T>::cplx) a = eadd(a, emul_i(op.w, xc));
+                a = esub(a, escale(cc[2 * (co - 1)].x, pc[o - LPC]));
+                a = esub(a, escale(cv.x, pc[o + LPC]));
+                a = esub(a, escale(cc[2 * (co - HX)].y, pc[o - HX * LPC]));
+                a = esub(a, escale(cv.y, pc[o + HX * LPC]));
+                a = esub(a, escale(cm[2 * co].z, pm[o]));
+                a = esub(a, escale(cv.z, pn[o]));
+                q[(int64_t)v * kp + cu] = a;
+                pq = eadd(pq, emul(xc, a));
+            }
+            __syncthreads();  // plane k-1's p_new slot is rewritten at the next conversion
+        }
+        if (failed) break;
+        // this item's per-lane sums into the CTA's column accumulators, in a fixed order
+        wsum[warp * 32 + lane] = ewide(pq);
+        __syncthreads();
+        if (threadIdx.x < KC) {
+            const int t = threadIdx.x;
+            double2 sm = make_double2(0.0, 0.0);
+            for (int w = 0; w < TY; ++w)
+                for (int h = 0; h < XS; ++h) {
+                    const double2 pw = wsum[w * 32 + h * LPC + t];
+                    sm.x += pw.x;
+                    sm.y += pw.y;
+                }
+            acc[c0 + t].x += sm.x;
+            acc[c0 + t].y += sm.y;
+        }
+        __syncthreads();
+    }
+
+    if (failed) {
+        if (threadIdx.x == 0) atomicExch(st.error, 1);
+        for (int b = 0; b < S; ++b)
+            if (pending & (1u << b)) mbar_wait(&bar[b], (parity >> b) & 1u);
+        __syncthreads();
+    }
+    for (int c = threadIdx.x; c < kp; c += blockDim.x) st.partA[(int64_t)blockIdx.x * kp + c] = acc[c];
+    const double2* totA;
+    const double* totB;
+    if (reduce_columns(st, true, false, kp, base, &totA, &totB)) {
+        stencil_finalise(st, totA, kp, hslot);
+        __syncthreads();
+        publish_counts(st, kp);
+    }
+}
+
 // Self-test of the bounded wait: one mbarrier that nothing ever arrives at, waited on
 // with a budget of `budget` cycles by one warp; the wait must give up and report.
 // Nothing is in flight, so giving up leaves no copy behind.
@@ -439,6 +653,122 @@ cudaError_t tma_stencil_launch(ElemKind inner, const OpRaw& o, const TmaStencil&
             k_pq_tma<float, 32><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st, slot);
         else
             k_pq_tma<float, 16><<<t.grid, THREADS, t.smem, s>>>(*tm, *tc, op, (float*)q, kp, t.zc, st, slot);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- fused direction + stencil (host)
+constexpr int kDpqStages = 2;
+
+bool dpq_eligible(ElemKind inner, int nx, int ny, int kp) {
+    const int kc = inner == EK_C64 ? 16 : 32;
+    return (inner == EK_C64 || inner == EK_F32) && nx % TX == 0 && ny % TY == 0 && kp % kc == 0 && kp <= 1024 &&
+           encode_fn() != nullptr;
+}
+
+template <typename T, int KC>
+static size_t dpq_smem(int kp) {
+    return 128 + (size_t)DpqLayout<T, KC, kDpqStages>::OFF_ACC + (size_t)kp * sizeof(double2);
+}
+
+template <typename T, int KC>
+static cudaError_t dpq_configure(size_t smem, int* per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_dpq_tma<T, KC, kDpqStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_dpq_tma<T, KC, kDpqStages>, THREADS, smem);
+    return e;
+}
+
+cudaError_t dpq_prepare(ElemKind inner, const DirRing& ring, const void* r, const void* cf8, int nx, int ny, int nz,
+                        int kp, int num_sms, TmaStencil* out) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc || !dpq_eligible(inner, nx, ny, kp) || !r || !cf8) return cudaErrorNotSupported;
+    if (ring.H < 1 || ring.H > kDirRingMax) return cudaErrorInvalidValue;
+    const bool cx = inner == EK_C64;
+    const size_t es = cx ? 8 : 4;
+    const int kc = cx ? 16 : 32;
+    const cuuint64_t dims[4] = {(cuuint64_t)kp, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[3] = {(cuuint64_t)kp * es, (cuuint64_t)kp * nx * es, (cuuint64_t)kp * nx * ny * es};
+    const cuuint32_t box[4] = {(cuuint32_t)kc, HX, HY, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt = cx ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    auto encode = [&](unsigned char* dst, const void* ptr) {
+        return enc(reinterpret_cast<CUtensorMap*>(dst), dt, 4, const_cast<void*>(ptr), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    };
+    if (encode(out->tmap_r, r) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    for (int sl = 0; sl < ring.H; ++sl) {
+        const void* p = static_cast<const unsigned char*>(ring.base) + (size_t)sl * ring.slot_elems * es;
+        if (encode(out->tmap_pf[sl], p) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    // 32-byte records {cx, cy, cz, dre, dinv (re, im or value, 0), 0, 0} per cell
+    const cuuint64_t cdims[4] = {8, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t cstrides[3] = {32, (cuuint64_t)nx * 32, (cuuint64_t)nx * ny * 32};
+    const cuuint32_t cbox[4] = {8, HX, HY, 1};
+    if (enc(reinterpret_cast<CUtensorMap*>(out->tmap_c8), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(cf8),
+            cdims, cstrides, cbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    out->kcf = kc;
+    out->smemf = cx ? dpq_smem<float2, 16>(kp) : dpq_smem<float, 32>(kp);
+    int per_sm = 0;
+    cudaError_t e = cx ? dpq_configure<float2, 16>(out->smemf, &per_sm) : dpq_configure<float, 32>(out->smemf, &per_sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // z-chunk length: whole waves of items against the two halo planes each chunk converts
+    const int tiles = (nx / TX) * (ny / TY) * (kp / kc);
+    const int grid_cap = per_sm * num_sms;
+    int best = nz;
+    double best_cost = 1e300;
+    for (int zc : {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, nz}) {
+        if (zc > nz || zc < 1) continue;
+        const long items = (long)tiles * ((nz + zc - 1) / zc);
+        const long grid = items < grid_cap ? items : grid_cap;
+        const double cost = (double)((items + grid - 1) / grid) * (zc + 2);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = zc;
+        }
+    }
+    out->zcf = best;
+    const long items = (long)tiles * ((nz + best - 1) / best);
+    out->gridf = (int)(items < grid_cap ? items : grid_cap);
+    out->fused = true;
+    return cudaSuccess;
+}
+
+cudaError_t dpq_launch(ElemKind inner, const OpRaw& o, const TmaStencil& t, const DirRing& ring, int slot, int prev,
+                       void* q, int kp, const ColState& st, cudaStream_t s) {
+    if (!t.fused || slot < 0 || slot >= ring.H || prev < 0 || prev >= ring.H) return cudaErrorInvalidValue;
+    const CUtensorMap* tr = reinterpret_cast<const CUtensorMap*>(t.tmap_r);
+    const CUtensorMap* tp = reinterpret_cast<const CUtensorMap*>(t.tmap_pf[prev]);
+    const CUtensorMap* tc = reinterpret_cast<const CUtensorMap*>(t.tmap_c8);
+    if (inner == EK_C64) {
+        Op<float2> op;
+        op.cf = static_cast<const Cf4<float>*>(o.cf);
+        op.dinv = static_cast<const float2*>(o.dinv);
+        op.w = (float)o.w;
+        op.nx = o.nx;
+        op.ny = o.ny;
+        op.nz = o.nz;
+        float2* pn = static_cast<float2*>(ring.base) + (size_t)slot * ring.slot_elems;
+        k_dpq_tma<float2, 16, kDpqStages><<<t.gridf, THREADS, t.smemf, s>>>(*tr, *tp, *tc, op, pn, (float2*)q, kp,
+                                                                           t.zcf, st, slot);
+    } else if (inner == EK_F32) {
+        Op<float> op;
+        op.cf = static_cast<const Cf4<float>*>(o.cf);
+        op.dinv = static_cast<const float*>(o.dinv);
+        op.w = 0.f;
+        op.nx = o.nx;
+        op.ny = o.ny;
+        op.nz = o.nz;
+        float* pn = static_cast<float*>(ring.base) + (size_t)slot * ring.slot_elems;
+        k_dpq_tma<float, 32, kDpqStages><<<t.gridf, THREADS, t.smemf, s>>>(*tr, *tp, *tc, op, pn, (float*)q, kp,
+                                                                          t.zcf, st, slot);
     } else {
         return cudaErrorInvalidValue;
     }

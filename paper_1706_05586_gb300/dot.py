@@ -80,7 +80,8 @@ class DotStats(C.Structure):
                 ("outer_steps", C.c_int32), ("status", C.c_int32), ("relres_max", C.c_double),
                 ("columns_solved", C.c_int64), ("block_solves", C.c_int64), ("ms_setup", C.c_double),
                 ("ms_solve", C.c_double), ("ms_post", C.c_double), ("kernel_launches", C.c_int64),
-                ("tuned_tma", C.c_int32), ("tuned_blocks_per_sm", C.c_int32)]
+                ("tuned_tma", C.c_int32), ("tuned_blocks_per_sm", C.c_int32), ("fused_direction", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -328,8 +329,10 @@ def dot_gradient_batch(ctxs, ngs, allow=()):
     return f, gs, rc
 
 
-def dot_set_stencil_path(ctx, tma):
-    return _check(load().dot_set_stencil_path(ctx, int(bool(tma))))
+def dot_set_stencil_path(ctx, mode):
+    """2: TMA stencil with the direction update fused in (default), 1: TMA stencil after a
+    separate direction pass, 0: direct-load stencil."""
+    return _check(load().dot_set_stencil_path(ctx, int(mode)))
 
 
 def dot_set_kernel_timing(ctx, enable):

@@ -5,6 +5,7 @@ bitwise identical to direct launches, and autotuned launches agree to rounding."
 import numpy as np
 import pytest
 
+from oracle import dot_oracle as orc
 from paper_1706_05586_gb300 import dot as D
 from paper_1706_05586_gb300 import synth
 from tests import problem
@@ -137,6 +138,9 @@ def test_stats_report_the_launch_configuration(problems):
         tma_ok = pb.wl.nx % 8 == 0 and pb.wl.ny % 8 == 0 and kp % 16 == 0
         assert st["tuned_blocks_per_sm"] == 5
         assert st["tuned_tma"] == (1 if tma_ok else 0)
+        # the direction update runs inside the TMA stencil where the tile width allows it
+        fused_ok = tma_ok and kp % (16 if pb.wl.omega_nu else 32) == 0
+        assert st["fused_direction"] == (1 if fused_ok else 0)
 
 
 @pytest.mark.parametrize("prec", [D.PREC_MIXED, D.PREC_FP64])
@@ -167,3 +171,39 @@ def test_direction_ring_rejects_other_sizes():
         assert e.value.code == D.DOT_EINVAL
     finally:
         D.dot_destroy(h)
+
+
+@pytest.mark.parametrize("prec,rtol,tol", [(D.PREC_MIXED, 1e-13, 1e-8), (D.PREC_FP64, 2e-15, 1e-10)])
+def test_batch_members_match_oracle(problems, prec, rtol, tol):
+    """Every member of a dot_gradient_batch call against the FP64 oracle (true relative f
+    and g at p0, the parity bars of the path), with a fourth member sampled as in the
+    batching workload: q = 2 optimized simultaneous sources and detectors from Algorithm 1
+    (dot_optimized_sampling, Sec. 3.2) completed by 6 random ones in the complementary
+    subspace (Eqs. (newW), (newV)), fed to dot_set_sampling."""
+    opt_pb = problems[2]                      # 16 x 16 physical sources and detectors, complex
+    rng = np.random.default_rng(31)
+    q, l = 2, 8
+    Yt = rng.standard_normal((opt_pb.wl.ns, l - q)) / np.sqrt(l - q)
+    Zt = rng.standard_normal((opt_pb.wl.nd, l - q)) / np.sqrt(l - q)
+    h = D.dot_create(0)
+    try:
+        configure(h, opt_pb, p=opt_pb.inp.p0, prec=D.PREC_FP64, rtol=1e-13)
+        W_opt, V_opt, _, _ = D.dot_optimized_sampling(h, q, q, opt_pb.wl.ns, opt_pb.wl.nd, l, l, Yt, Zt)
+    finally:
+        D.dot_destroy(h)
+    members = [(pb, pb.inp.W, pb.inp.V) for pb in problems] + [(opt_pb, W_opt, V_opt)]
+    hs = [D.dot_create(0) for _ in members]
+    try:
+        for h, (pb, W, V) in zip(hs, members):
+            configure(h, pb, p=pb.inp.p0, prec=prec, rtol=rtol, W=W, V=V)
+        f, gs, rc = D.dot_gradient_batch(hs, [pb.wl.np_ for pb, _, _ in members])
+        assert rc == D.DOT_OK
+    finally:
+        for h in hs:
+            D.dot_destroy(h)
+    for i, (pb, W, V) in enumerate(members):
+        mu = pb.mu_of(pb.inp.p0)
+        ref = orc.evaluate(pb.D, mu, pb.grid, pb.wl.bc, pb.wl.omega_nu, pb.Bd, pb.Cd, pb.M, W, V,
+                           dmu=pb.dmu_of(pb.inp.p0))
+        assert abs(f[i] - ref["f"]) <= tol * ref["f"], i
+        assert rel(gs[i], ref["g_p"]) <= tol, i

@@ -61,7 +61,7 @@ def test_absorption_on_sampled_cells(setup):
 
 def test_launch_configuration(setup):
     st = setup["st"]
-    assert st["tuned_tma"] == 1 and st["k"] == 16
+    assert st["tuned_tma"] == 1 and st["fused_direction"] == 1 and st["k"] == 16
     assert st["relres_max"] <= RTOL
 
 

@@ -300,20 +300,31 @@ def test_forward_model_all_sources(name, ctx):
 @pytest.mark.parametrize("name", ["cplx_24x16x10_k32", "real_16x16x9_k32", "cplx_16x24x8_k48", "real_24x8x7_k16",
                                   "real_16x16x1_k32", "cplx_8x8x6_k256", "real_16x8x5_k64"])
 def test_tma_stencil_matches_direct_load_kernel(name, ctx):
-    """The TMA-staged stencil and the direct-load stencil give the same solve to rounding."""
+    """The three stencil paths (direction update fused into the TMA stencil, TMA stencil
+    after a separate direction pass, direct loads) give the same solve to rounding (their
+    column sums p^T q add in different orders); the fused path runs on every case whose
+    padded width is a multiple of 16 (complex) or 32 (real) columns."""
     pb, ref = _case(name)
     out = {}
-    for tma in (1, 0):
-        configure(ctx, pb, p=pb.inp.p0, prec=D.PREC_MIXED, rtol=1e-13)
-        D.dot_set_stencil_path(ctx, tma)
-        f, g, rc = D.dot_gradient(ctx, pb.wl.np_)
-        assert rc == D.DOT_OK
-        out[tma] = (f, g, D.dot_get_stats(ctx)["iters_max"])
-    D.dot_set_stencil_path(ctx, 1)
-    assert abs(out[1][0] - out[0][0]) <= 1e-10 * abs(out[0][0])
-    assert rel(out[1][1], out[0][1]) <= 1e-9
-    assert abs(out[1][2] - out[0][2]) <= 3
-    assert abs(out[1][0] - ref["f"]) <= 1e-8 * ref["f"]
+    try:
+        for mode in (2, 1, 0):
+            configure(ctx, pb, p=pb.inp.p0, prec=D.PREC_MIXED, rtol=1e-13)
+            D.dot_set_stencil_path(ctx, mode)
+            f, g, rc = D.dot_gradient(ctx, pb.wl.np_)
+            assert rc == D.DOT_OK
+            st = D.dot_get_stats(ctx)
+            out[mode] = (f, g, st["iters_max"], st["fused_direction"], st["tuned_tma"])
+    finally:
+        D.dot_set_stencil_path(ctx, 2)
+    kp = -(-(pb.wl.ls + pb.wl.ld) // 4) * 4
+    fused_ok = kp % (16 if _cplx(pb) else 32) == 0
+    assert out[2][3] == (1 if fused_ok else 0) and out[1][3] == 0 and out[0][3] == 0
+    assert out[2][4] == 1 and out[1][4] == 1 and out[0][4] == 0
+    for m in (2, 1):
+        assert abs(out[m][0] - out[0][0]) <= 1e-10 * abs(out[0][0])
+        assert rel(out[m][1], out[0][1]) <= 1e-9
+        assert abs(out[m][2] - out[0][2]) <= 3
+        assert abs(out[m][0] - ref["f"]) <= 1e-8 * ref["f"]
 
 
 @pytest.mark.parametrize("prec", [D.PREC_FP64, D.PREC_MIXED])
