@@ -80,15 +80,25 @@ __device__ __forceinline__ void tma_load4(const CUtensorMap* tm, void* dst, uint
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load3(const CUtensorMap* tm, void* dst, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // One plane of the tile into one ring slot: p box {KC, HX, HY, 1} at (c0, i0 - 1,
-// j0 - 1, z), then the coefficient box {4, HX, HY, 1} at (0, i0 - 1, j0 - 1, z)
-// right behind it; both complete on the slot's mbarrier.
+// j0 - 1, z), then the coefficients right behind it; both complete on the slot's
+// mbarrier.  The coefficient map views each grid row as one run of 4 nx floats, so a
+// plane's 10 x 10 cells arrive as 10 rows of 160 contiguous bytes (x coordinate
+// 4 (i0 - 1): a multiple of 16 bytes), laid out in shared memory exactly as cells.
 __device__ __forceinline__ void tma_plane(const CUtensorMap* tm, const CUtensorMap* tc, unsigned char* dst,
                                           uint32_t p_bytes, uint64_t* bar, int c0, int x, int y, int z) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, p_bytes + CF_BYTES);
     tma_load4(tm, dst, bar, c0, x, y, z);
-    tma_load4(tc, dst + p_bytes, bar, 0, x, y, z);
+    tma_load3(tc, dst + p_bytes, bar, 4 * x, y, z);
 }
 
 // Two adjacent real columns carried by one lane (FP32 tiles of 64 columns, so that a
@@ -323,11 +333,18 @@ struct DpqLayout {
     static constexpr int OFF_BAR = OFF_CF + NCF * C8_SLOT;     // S mbarriers
     static constexpr int OFF_ACC = OFF_BAR + (S * 8 + 15) / 16 * 16;  // kp column accumulators
     static_assert(P_BYTES % 128 == 0 && C8_SLOT % 128 == 0, "TMA destinations on 128-byte boundaries");
-    static_assert(TY * 32 * (int)sizeof(double2) <= 2 * P_BYTES, "per-warp partials fit in staging slot 0");
 };
 
 __device__ __forceinline__ float dinv_of(float4 w, float*) { return w.x; }
 __device__ __forceinline__ float2 dinv_of(float4 w, float2*) { return make_float2(w.x, w.y); }
+
+// 16 bytes of consecutive columns carried by one lane of the fused kernel: two
+// complex64 or four FP32 columns, moved by one shared-memory or global access.
+template <typename T>
+struct alignas(16) Pack16 {
+    static constexpr int N = 16 / (int)sizeof(T);
+    T e[N];
+};
 
 template <typename T, int KC, int S>
 __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ CUtensorMap tr,
@@ -336,21 +353,25 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
                                                         T* __restrict__ p_new, T* __restrict__ q, int kp,
                                                         int zc_len, ColState st, int hslot) {
     using Ly = DpqLayout<T, KC, S>;
-    constexpr int LPC = KC;           // lanes per cell, one column each
+    using P = Pack16<T>;
+    constexpr int CPL = P::N;         // columns per lane
+    constexpr int LPC = KC / CPL;     // lanes per cell
     constexpr int XS = 32 / LPC;      // cells per warp instruction
-    static_assert(LPC == 16 || LPC == 32, "column tile");
+    static_assert(LPC == 8, "column tile of 128 bytes");
     constexpr int PLANE = Ly::PLANE;
     constexpr int P_BYTES = Ly::P_BYTES;
+    constexpr int PLANE_P = PLANE / CPL;  // 16-byte units of one plane
     unsigned char* base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-    T* pn_ring = reinterpret_cast<T*>(base + Ly::OFF_PN);
+    P* pn_ring = reinterpret_cast<P*>(base + Ly::OFF_PN);
     unsigned char* stg = base + Ly::OFF_ST;
     unsigned char* cfr = base + Ly::OFF_CF;
     uint64_t* bar = reinterpret_cast<uint64_t*>(base + Ly::OFF_BAR);
     double2* acc = reinterpret_cast<double2*>(base + Ly::OFF_ACC);
     double2* wsum = reinterpret_cast<double2*>(stg);
+    static_assert(TY * 32 * CPL * (int)sizeof(double2) <= 2 * P_BYTES, "per-lane partials fit in staging slot 0");
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int col = lane % LPC, xsub = lane / LPC;
+    const int lc = lane % LPC, xsub = lane / LPC;  // the lane's columns CPL lc .. CPL lc + CPL - 1 of the tile
     const int nx = op.nx, ny = op.ny, nz = op.nz;
     const int tiles_x = nx / TX, tiles_y = ny / TY, tiles_c = kp / KC;
     const int zchunks = (nz + zc_len - 1) / zc_len;
@@ -368,21 +389,32 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
     bool failed = false;
 
     for (int item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
+        // column tiles fastest: the tiles sharing a cell's columns run on neighbouring
+        // CTAs at the same time, so the 256-byte L2 lines their 128-byte rows split are
+        // used by both while resident
         int rem = item;
+        const int cci = rem % tiles_c;
+        rem /= tiles_c;
         const int txi = rem % tiles_x;
         rem /= tiles_x;
         const int tyi = rem % tiles_y;
-        rem /= tiles_y;
-        const int cci = rem % tiles_c;
-        const int zci = rem / tiles_c;
+        const int zci = rem / tiles_y;
         const int i0 = txi * TX, j0 = tyi * TY, c0 = cci * KC;
         const int z0 = zci * zc_len, z1 = min(z0 + zc_len, nz);
-        const int cu = c0 + col;
-        const bool act = st.active[cu] != 0;
-        const bool run = act && !st.upd[cu];
+        const int cb = c0 + CPL * lc;   // the lane's first column
+        bool run[CPL];
+        T bt[CPL];
+        bool act = false, anyrun = false;
+#pragma unroll
+        for (int u = 0; u < CPL; ++u) {
+            const bool a = st.active[cb + u] != 0;
+            run[u] = a && !st.upd[cb + u];
+            bt[u] = run[u] ? enarrow<T>(st.beta[cb + u]) : ezero<T>();
+            act = act || a;
+            anyrun = anyrun || run[u];
+        }
         // a tile whose columns have all stopped needs neither p_new nor q
         if (!__syncthreads_or(act)) continue;
-        const T bt = run ? enarrow<T>(st.beta[cu]) : ezero<T>();
 
         // planes z0-1 .. z1 (z1 is the halo below the chunk; zero-filled past the grid)
         auto sslot = [&](int z) { return (z - z0 + 1) % S; };
@@ -395,7 +427,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
             mbar_expect_tx(&bar[sl], 2 * P_BYTES + Ly::C8_BYTES);
             tma_load4(&tr, d, &bar[sl], c0, i0 - 1, j0 - 1, z);
             tma_load4(&tp, d + P_BYTES, &bar[sl], c0, i0 - 1, j0 - 1, z);
-            tma_load4(&tc8, cfr + (size_t)cslot(z) * Ly::C8_SLOT, &bar[sl], 0, i0 - 1, j0 - 1, z);
+            tma_load3(&tc8, cfr + (size_t)cslot(z) * Ly::C8_SLOT, &bar[sl], 8 * (i0 - 1), j0 - 1, z);
         };
         // (the barrier above also ends the previous item's reads of the partials in slot 0)
         for (int z = z0 - 1; z <= min(z0 - 2 + S, z1); ++z) {
@@ -413,21 +445,28 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
                 pending &= ~(1u << sl);
             }
             if (__syncthreads_or(!ok)) return false;
-            const T* Rr = reinterpret_cast<const T*>(stg + (size_t)sl * 2 * P_BYTES);
-            const T* Po = reinterpret_cast<const T*>(stg + (size_t)sl * 2 * P_BYTES + P_BYTES);
+            const P* Rr = reinterpret_cast<const P*>(stg + (size_t)sl * 2 * P_BYTES);
+            const P* Po = reinterpret_cast<const P*>(stg + (size_t)sl * 2 * P_BYTES + P_BYTES);
             const float4* cw = reinterpret_cast<const float4*>(cfr + (size_t)cslot(z) * Ly::C8_SLOT);
-            T* Pn = pn_ring + pslot(z) * PLANE;
+            P* Pn = pn_ring + pslot(z) * PLANE_P;
             const bool own = z >= z0 && z < z1;
+            const int64_t zoff = (int64_t)nx * ny * z;
             for (int cell = warp * XS + xsub; cell < HX * HY; cell += TY * XS) {
-                const int o = cell * LPC + col;
-                const T po = Po[o];
-                T pn = po;
-                if (run) pn = eadd(emul(dinv_of(cw[2 * cell + 1], (T*)nullptr), Rr[o]), emul(bt, po));
+                const int o = cell * LPC + lc;
+                const P po = Po[o];
+                P pn = po;
+                if (anyrun) {
+                    const T dv = dinv_of(cw[2 * cell + 1], (T*)nullptr);
+                    const P rr = Rr[o];
+#pragma unroll
+                    for (int u = 0; u < CPL; ++u)
+                        if (run[u]) pn.e[u] = eadd(emul(dv, rr.e[u]), emul(bt[u], po.e[u]));
+                }
                 Pn[o] = pn;
                 const int hy = cell / HX, hx = cell - hy * HX;
                 if (own && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
-                    const int64_t v = (int64_t)(i0 + hx - 1) + (int64_t)nx * ((j0 + hy - 1) + (int64_t)ny * z);
-                    p_new[v * kp + cu] = pn;
+                    const int64_t v = zoff + (int64_t)(i0 + hx - 1) + (int64_t)nx * (j0 + hy - 1);
+                    *reinterpret_cast<P*>(p_new + v * kp + cb) = pn;
                 }
             }
             __syncthreads();  // staging slot read, p_new plane written
@@ -438,15 +477,17 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
             return true;
         };
         failed = !convert(z0 - 1) || !convert(z0);
-        T pq = ezero<T>();
+        T pq[CPL];
+#pragma unroll
+        for (int u = 0; u < CPL; ++u) pq[u] = ezero<T>();
         for (int k = z0; k < z1 && !failed; ++k) {
             if (!convert(k + 1)) {
                 failed = true;
                 break;
             }
-            const T* pm = pn_ring + pslot(k - 1) * PLANE;
-            const T* pc = pn_ring + pslot(k) * PLANE;
-            const T* pn = pn_ring + pslot(k + 1) * PLANE;
+            const P* pm = pn_ring + pslot(k - 1) * PLANE_P;
+            const P* pc = pn_ring + pslot(k) * PLANE_P;
+            const P* pn = pn_ring + pslot(k + 1) * PLANE_P;
             const float4* cm = reinterpret_cast<const float4*>(cfr + (size_t)cslot(k - 1) * Ly::C8_SLOT);
             const float4* cc = reinterpret_cast<const float4*>(cfr + (size_t)cslot(k) * Ly::C8_SLOT);
             const int j = j0 + warp;
@@ -456,33 +497,42 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
             for (int xi = xsub; xi < TX; xi += XS) {
                 const int i = i0 + xi;
                 const int v = i + nx * (j + ny * k);
-                const int o = row + (xi + 1) * LPC + col;
+                const int o = row + (xi + 1) * LPC + lc;
                 const int co = crow + xi + 1;
                 const float4 cv = cc[2 * co];   // (cx, cy, cz, dre)
-                const T xc = pc[o];
-                T a = escale(cv.w, xc);
-                if constexpr (Elem<T>::cplx) a = eadd(a, emul_i(op.w, xc));
-                a = esub(a, escale(cc[2 * (co - 1)].x, pc[o - LPC]));
-                a = esub(a, escale(cv.x, pc[o + LPC]));
-                a = esub(a, escale(cc[2 * (co - HX)].y, pc[o - HX * LPC]));
-                a = esub(a, escale(cv.y, pc[o + HX * LPC]));
-                a = esub(a, escale(cm[2 * co].z, pm[o]));
-                a = esub(a, escale(cv.z, pn[o]));
-                q[(int64_t)v * kp + cu] = a;
-                pq = eadd(pq, emul(xc, a));
+                const float cxm = cc[2 * (co - 1)].x, cym = cc[2 * (co - HX)].y, czm = cm[2 * co].z;
+                const P xc = pc[o];
+                const P xw = pc[o - LPC], xe = pc[o + LPC], xs = pc[o - HX * LPC], xn = pc[o + HX * LPC];
+                const P xd = pm[o], xu = pn[o];
+                P a;
+#pragma unroll
+                for (int u = 0; u < CPL; ++u) {
+                    T t = escale(cv.w, xc.e[u]);
+                    if constexpr (Elem<T>::cplx) t = eadd(t, emul_i(op.w, xc.e[u]));
+                    t = esub(t, escale(cxm, xw.e[u]));
+                    t = esub(t, escale(cv.x, xe.e[u]));
+                    t = esub(t, escale(cym, xs.e[u]));
+                    t = esub(t, escale(cv.y, xn.e[u]));
+                    t = esub(t, escale(czm, xd.e[u]));
+                    t = esub(t, escale(cv.z, xu.e[u]));
+                    a.e[u] = t;
+                    pq[u] = eadd(pq[u], emul(xc.e[u], t));
+                }
+                *reinterpret_cast<P*>(q + (int64_t)v * kp + cb) = a;
             }
             __syncthreads();  // plane k-1's p_new slot is rewritten at the next conversion
         }
         if (failed) break;
         // this item's per-lane sums into the CTA's column accumulators, in a fixed order
-        wsum[warp * 32 + lane] = ewide(pq);
+#pragma unroll
+        for (int u = 0; u < CPL; ++u) wsum[(warp * 32 + lane) * CPL + u] = ewide(pq[u]);
         __syncthreads();
         if (threadIdx.x < KC) {
-            const int t = threadIdx.x;
+            const int t = threadIdx.x, tl = t / CPL, tu = t % CPL;
             double2 sm = make_double2(0.0, 0.0);
             for (int w = 0; w < TY; ++w)
                 for (int h = 0; h < XS; ++h) {
-                    const double2 pw = wsum[w * 32 + h * LPC + t];
+                    const double2 pw = wsum[(w * 32 + h * LPC + tl) * CPL + tu];
                     sm.x += pw.x;
                     sm.y += pw.y;
                 }
@@ -551,10 +601,15 @@ static size_t tma_smem(size_t es, int kc, int kp) {
            (size_t)kp * sizeof(double2);
 }
 
-// Shared-memory opt-in and resident blocks per SM of one instantiation.
+// Shared-memory opt-in and resident blocks per SM of one instantiation.  The opt-in is
+// a property of the kernel, shared by every context of the process, so it is set to
+// what the widest block (1024 columns) needs: a context preparing a narrower block must
+// not lower it under another context's launches.  Occupancy follows the actual size.
 template <typename T, int KC>
 static cudaError_t tma_configure(size_t smem, int* per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_pq_tma<T, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t widest = tma_smem(sizeof(T), KC == 64 ? 64 : KC, 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_pq_tma<T, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(smem > widest ? smem : widest));
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pq_tma<T, KC>, THREADS, smem);
     return e;
 }
@@ -580,10 +635,11 @@ cudaError_t tma_stencil_prepare(ElemKind inner, const DirRing& ring, const void*
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
     // packed coefficients {cx, cy, cz, dre} per cell, FP32 for both recurrence types
-    const cuuint64_t cdims[4] = {4, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    const cuuint64_t cstrides[3] = {16, (cuuint64_t)nx * 16, (cuuint64_t)nx * ny * 16};
-    const cuuint32_t cbox[4] = {4, HX, HY, 1};
-    const CUresult rc = enc(reinterpret_cast<CUtensorMap*>(out->tmap_cf), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+    // viewed as [z][y][4 nx floats]: a box of 4 HX floats x HY rows is the plane's cells
+    const cuuint64_t cdims[3] = {(cuuint64_t)nx * 4, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t cstrides[2] = {(cuuint64_t)nx * 16, (cuuint64_t)nx * ny * 16};
+    const cuuint32_t cbox[3] = {4 * HX, HY, 1};
+    const CUresult rc = enc(reinterpret_cast<CUtensorMap*>(out->tmap_cf), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                             const_cast<void*>(cf), cdims, cstrides, cbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -673,10 +729,12 @@ static size_t dpq_smem(int kp) {
     return 128 + (size_t)DpqLayout<T, KC, kDpqStages>::OFF_ACC + (size_t)kp * sizeof(double2);
 }
 
+// As tma_configure: the opt-in covers the widest block, whichever context sets it.
 template <typename T, int KC>
 static cudaError_t dpq_configure(size_t smem, int* per_sm) {
+    const size_t widest = dpq_smem<T, KC>(1024);
     cudaError_t e = cudaFuncSetAttribute(k_dpq_tma<T, KC, kDpqStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)(smem > widest ? smem : widest));
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_dpq_tma<T, KC, kDpqStages>, THREADS, smem);
     return e;
@@ -706,10 +764,11 @@ cudaError_t dpq_prepare(ElemKind inner, const DirRing& ring, const void* r, cons
         if (encode(out->tmap_pf[sl], p) != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
     // 32-byte records {cx, cy, cz, dre, dinv (re, im or value, 0), 0, 0} per cell
-    const cuuint64_t cdims[4] = {8, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    const cuuint64_t cstrides[3] = {32, (cuuint64_t)nx * 32, (cuuint64_t)nx * ny * 32};
-    const cuuint32_t cbox[4] = {8, HX, HY, 1};
-    if (enc(reinterpret_cast<CUtensorMap*>(out->tmap_c8), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(cf8),
+    // viewed as [z][y][8 nx floats]: each plane of the tile arrives as HY rows of 320 bytes
+    const cuuint64_t cdims[3] = {(cuuint64_t)nx * 8, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t cstrides[2] = {(cuuint64_t)nx * 32, (cuuint64_t)nx * ny * 32};
+    const cuuint32_t cbox[3] = {8 * HX, HY, 1};
+    if (enc(reinterpret_cast<CUtensorMap*>(out->tmap_c8), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(cf8),
             cdims, cstrides, cbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
