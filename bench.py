@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-batch8", action="store_true",
                     help="skip the short eight-inversion batch measurement the default line carries")
+    ap.add_argument("--stencil-path", type=int, choices=(0, 1, 2), default=2,
+                    help="2: direction update fused into the TMA stencil (default), 1: TMA stencil after a "
+                         "separate direction pass, 0: direct-load stencil")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library time its launch variants on the first solve and keep the fastest")
     ap.add_argument("--api", choices=("abi", "autograd"), default="abi",
@@ -220,6 +223,7 @@ def run_ours(args):
     D.dot_set_stream(ctx, stream.cuda_stream)
     Dfield, M = setup_problem(D, ctx, wl, inp, args.precision, args.rtol, log)
     D.dot_set_launch_options(ctx, True, args.autotune)
+    D.dot_set_stencil_path(ctx, args.stencil_path)
     ps = p_sequence(inp, args.warmup + args.steps)
     p_dev = torch.tensor(np.stack(ps), dtype=torch.float64, device=f"cuda:{local}")
     pals = (synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
@@ -416,7 +420,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
     # the eight-inversion batch workload, briefly, so that the same record carries it
     if ws == 1 and not args.no_batch8 and args.api == "abi":
-        b8 = batch_measure(2, 2, args.rtol, log)
+        b8 = batch_measure(2, 2, args.rtol, log, args.stencil_path)
         out["batch8"] = {k: b8[k] for k in ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "clocks",
                                             "gpu_launches", "roofline")}
         out["batch8"]["config"] = {k: b8["config"][k] for k in ("grids", "omega_over_nu", "ls", "ld", "rtol", "iters",
@@ -530,7 +534,7 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def batch_measure(steps, warmup, rtol, log):
+def batch_measure(steps, warmup, rtol, log, stencil_path=2):
     """Eight independent inversions with uneven grids and mixed omega (synth.BATCH8) per
     step through dot_gradient_batch, autotuned launches and graph-replayed iteration
     batches; the timed region is bracketed by device synchronisation on the host clock
@@ -558,6 +562,7 @@ def batch_measure(steps, warmup, rtol, log):
         D.dot_set_sampling(h, inp.W, inp.V)
         D.dot_set_solver(h, D.PREC_MIXED, rtol, 0)
         D.dot_set_launch_options(h, True, True)
+        D.dot_set_stencil_path(h, stencil_path)
         hs.append(h)
         ps = p_sequence(inp, warmup + steps)
         pdev.append(torch.tensor(np.stack(ps), dtype=torch.float64, device="cuda:0"))
@@ -627,7 +632,7 @@ def run_batch(args):
     import torch
     torch.cuda.set_device(0)
     log = lambda m: print(f"[bench] {m}", file=sys.stderr, flush=True)
-    print(json.dumps(batch_measure(args.steps, args.warmup, args.rtol, log)), flush=True)
+    print(json.dumps(batch_measure(args.steps, args.warmup, args.rtol, log, args.stencil_path)), flush=True)
 
 
 def main():

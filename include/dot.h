@@ -221,7 +221,9 @@ int dot_get_stats(dot_ctx* ctx, dot_stats* stats);
  * batch of Krylov iterations from a CUDA graph captured on the context stream (the
  * stream must be capturable: not the legacy default stream, no other thread queuing
  * on it meanwhile).  autotune != 0 (default 0) times the first batches of a solve with
- * each stencil path and 4, 5, 8 or 16 blocks per SM for the vector kernels, keeps the
+ * each stencil path that dot_set_stencil_path allows (direct loads; TMA stencil; TMA
+ * stencil with the direction update fused in) and 4, 5, 8 or 16 blocks per SM for the
+ * vector kernels, keeps the
  * fastest for the rest of the solve and for later solves of the same shape; since the
  * reduction order follows the launch shape, results then agree to rounding (not
  * bitwise) with an untuned run. */

@@ -94,8 +94,9 @@ void release(DevBuf& b) {
 }
 
 struct Tuning {
-    bool tma;
-    int blocks_per_sm;
+    bool tma;            // TMA-staged stencil
+    int blocks_per_sm;   // vector kernels
+    bool fused = false;  // direction update inside the TMA stencil
 };
 
 // Host-side state of one block solve in progress.
@@ -117,7 +118,7 @@ struct SolveRun {
     int maxit = 0;
     int it = 0, act = 0, upd = 0;
     bool first = true;
-    Tuning cfg{true, 8};
+    Tuning cfg{true, 8, false};
     // autotuning: candidates tried one batch each, then the fastest is kept
     std::vector<Tuning> cands;
     std::vector<float> cand_ms;
@@ -143,6 +144,7 @@ struct TunedChoice {
     int kp = 0, inner = 0;
     bool tma = true;
     int blocks_per_sm = 8;
+    bool fused = false;
     float ms = 0.f;
 };
 
@@ -212,7 +214,7 @@ struct dot_ctx {
     bool use_graphs = true;
     bool autotune = false;
     TunedChoice tuned;
-    Tuning last_cfg{false, -1};  // launch configuration of the last solve (blocks_per_sm -1: none yet)
+    Tuning last_cfg{false, -1, false};  // launch configuration of the last solve (blocks_per_sm -1: none yet)
     bool last_fused = false;     // the last solve ran the direction update inside the stencil
     int ring_cap = kDirRingMax;  // most direction-ring slots to try (dot_set_direction_ring)
     cudaEvent_t bev[2] = {nullptr, nullptr};
@@ -415,7 +417,7 @@ int apply_tuning(dot_ctx* c, SolveRun& r, const Tuning& t) {
             CK(dpq_prepare(r.inner, r.ring, c->ri.p, c->cf8.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma));
         r.tma_ready = true;
     }
-    r.fused = t.tma && r.tma.fused;
+    r.fused = t.tma && t.fused && r.tma.fused;
     run_release_graph(r);
     r.graph_failed = false;
     return DOT_OK;
@@ -454,16 +456,19 @@ int solve_begin(dot_ctx* c, int kp, int kr) {
     r.o64 = op64(c);
     r.delta = r.mixed ? c->delta : 0.0;
     r.maxit = c->maxit > 0 ? c->maxit : 10 * (c->nx + c->ny + c->nz);
-    const bool tma_ok = tma_stencil_eligible(r.inner, c->nx, c->ny, kp);
-    Tuning base{c->stencil_mode != 0 && tma_ok, 5};  // five 256-thread blocks per SM: one wave at the update kernel's register limit
+    const bool tma_ok = c->stencil_mode != 0 && tma_stencil_eligible(r.inner, c->nx, c->ny, kp);
+    const bool fused_ok = tma_ok && c->stencil_mode == 2 && dpq_eligible(r.inner, c->nx, c->ny, kp);
+    // five 256-thread blocks per SM: one wave at the update kernel's register limit
+    Tuning base{tma_ok, 5, fused_ok};
     if (c->autotune) {
         const bool have = c->tuned.valid && c->tuned.n == r.n && c->tuned.kp == kp && c->tuned.inner == (int)r.inner;
         if (have) {
-            base = Tuning{c->tuned.tma && tma_ok, c->tuned.blocks_per_sm};
+            base = Tuning{c->tuned.tma && tma_ok, c->tuned.blocks_per_sm, c->tuned.fused && fused_ok};
         } else {
             for (int bps : {4, 5, 8, 16}) {
-                r.cands.push_back(Tuning{false, bps});
-                if (tma_ok) r.cands.push_back(Tuning{true, bps});
+                r.cands.push_back(Tuning{false, bps, false});
+                if (tma_ok) r.cands.push_back(Tuning{true, bps, false});
+                if (fused_ok) r.cands.push_back(Tuning{true, bps, true});
             }
             r.cand_ms.assign(r.cands.size(), 0.f);
             r.cand_at = 0;
@@ -558,6 +563,7 @@ int solve_poll(dot_ctx* c) {
             c->tuned.kp = r.kp;
             c->tuned.inner = (int)r.inner;
             c->tuned.tma = r.cands[best].tma;
+            c->tuned.fused = r.cands[best].fused;
             c->tuned.blocks_per_sm = r.cands[best].blocks_per_sm;
             c->tuned.ms = r.cand_ms[best];
             r.cand_at = -1;

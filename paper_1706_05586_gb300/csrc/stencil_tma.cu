@@ -434,17 +434,15 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
             if (threadIdx.x == 0) issue(z);
             pending |= 1u << sslot(z);
         }
-        // wait for plane z, convert it into its p_new slot (and, for the chunk's own
-        // planes, write the tile's cells to the ring slot in global memory), then hand
-        // the staging slot to plane z + S
+        // wait for plane z and convert it into its p_new slot (and, for the chunk's own
+        // planes, write the tile's cells to the ring slot in global memory); no barrier:
+        // the caller's next barrier ends the reads of the staging slot
         auto convert = [&](int z) -> bool {
             const int sl = sslot(z);
             const bool ok = mbar_wait(&bar[sl], (parity >> sl) & 1u);
-            if (ok) {
-                parity ^= 1u << sl;
-                pending &= ~(1u << sl);
-            }
-            if (__syncthreads_or(!ok)) return false;
+            if (!ok) return false;
+            parity ^= 1u << sl;
+            pending &= ~(1u << sl);
             const P* Rr = reinterpret_cast<const P*>(stg + (size_t)sl * 2 * P_BYTES);
             const P* Po = reinterpret_cast<const P*>(stg + (size_t)sl * 2 * P_BYTES + P_BYTES);
             const float4* cw = reinterpret_cast<const float4*>(cfr + (size_t)cslot(z) * Ly::C8_SLOT);
@@ -469,58 +467,89 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
                     *reinterpret_cast<P*>(p_new + v * kp + cb) = pn;
                 }
             }
-            __syncthreads();  // staging slot read, p_new plane written
+            return true;
+        };
+        // after a barrier that ends every read of plane z's staging slot: refill it
+        auto refill = [&](int z) {
             if (z + S <= z1) {
                 if (threadIdx.x == 0) issue(z + S);
                 pending |= 1u << sslot(z + S);
             }
-            return true;
         };
-        failed = !convert(z0 - 1) || !convert(z0);
+        // the lane's own cells of its tile row: x = xsub + XS t; their -z neighbours
+        // (p_new and the face coefficient of the plane below) stay in registers from
+        // one plane to the next, so a plane's compute reads only planes k and k + 1
+        constexpr int NT = TX / XS;
+        const int j = j0 + warp;
+        const int row = (warp + 1) * HX * LPC;
+        const int crow = (warp + 1) * HX;
+        P xd[NT];
+        float czd[NT];
         T pq[CPL];
 #pragma unroll
         for (int u = 0; u < CPL; ++u) pq[u] = ezero<T>();
-        for (int k = z0; k < z1 && !failed; ++k) {
-            if (!convert(k + 1)) {
-                failed = true;
-                break;
-            }
-            const P* pm = pn_ring + pslot(k - 1) * PLANE_P;
-            const P* pc = pn_ring + pslot(k) * PLANE_P;
-            const P* pn = pn_ring + pslot(k + 1) * PLANE_P;
-            const float4* cm = reinterpret_cast<const float4*>(cfr + (size_t)cslot(k - 1) * Ly::C8_SLOT);
-            const float4* cc = reinterpret_cast<const float4*>(cfr + (size_t)cslot(k) * Ly::C8_SLOT);
-            const int j = j0 + warp;
-            const int row = (warp + 1) * HX * LPC;
-            const int crow = (warp + 1) * HX;
-#pragma unroll 2
-            for (int xi = xsub; xi < TX; xi += XS) {
-                const int i = i0 + xi;
-                const int v = i + nx * (j + ny * k);
-                const int o = row + (xi + 1) * LPC + lc;
-                const int co = crow + xi + 1;
-                const float4 cv = cc[2 * co];   // (cx, cy, cz, dre)
-                const float cxm = cc[2 * (co - 1)].x, cym = cc[2 * (co - HX)].y, czm = cm[2 * co].z;
-                const P xc = pc[o];
-                const P xw = pc[o - LPC], xe = pc[o + LPC], xs = pc[o - HX * LPC], xn = pc[o + HX * LPC];
-                const P xd = pm[o], xu = pn[o];
-                P a;
+        bool ok = convert(z0 - 1);
+        failed = __syncthreads_or(!ok);
+        if (!failed) {
+            refill(z0 - 1);
+            const P* pl = pn_ring + pslot(z0 - 1) * PLANE_P;
+            const float4* cl = reinterpret_cast<const float4*>(cfr + (size_t)cslot(z0 - 1) * Ly::C8_SLOT);
 #pragma unroll
-                for (int u = 0; u < CPL; ++u) {
-                    T t = escale(cv.w, xc.e[u]);
-                    if constexpr (Elem<T>::cplx) t = eadd(t, emul_i(op.w, xc.e[u]));
-                    t = esub(t, escale(cxm, xw.e[u]));
-                    t = esub(t, escale(cv.x, xe.e[u]));
-                    t = esub(t, escale(cym, xs.e[u]));
-                    t = esub(t, escale(cv.y, xn.e[u]));
-                    t = esub(t, escale(czm, xd.e[u]));
-                    t = esub(t, escale(cv.z, xu.e[u]));
-                    a.e[u] = t;
-                    pq[u] = eadd(pq[u], emul(xc.e[u], t));
-                }
-                *reinterpret_cast<P*>(q + (int64_t)v * kp + cb) = a;
+            for (int t = 0; t < NT; ++t) {
+                const int xi = xsub + XS * t;
+                xd[t] = pl[row + (xi + 1) * LPC + lc];
+                czd[t] = cl[2 * (crow + xi + 1)].z;
             }
-            __syncthreads();  // plane k-1's p_new slot is rewritten at the next conversion
+            ok = convert(z0);
+            failed = __syncthreads_or(!ok);
+        }
+        if (!failed) {
+            refill(z0);
+            ok = convert(z0 + 1);
+            failed = __syncthreads_or(!ok);
+        }
+        if (!failed) refill(z0 + 1);
+        for (int k = z0; k < z1 && !failed; ++k) {
+            // plane k + 2 goes into the slot plane k - 1 left (its values the stencil needs
+            // are the registers xd, czd) while plane k is computed from planes k and k + 1
+            ok = k + 2 > z1 || convert(k + 2);
+            if (ok) {
+                const P* pc = pn_ring + pslot(k) * PLANE_P;
+                const P* pn = pn_ring + pslot(k + 1) * PLANE_P;
+                const float4* cc = reinterpret_cast<const float4*>(cfr + (size_t)cslot(k) * Ly::C8_SLOT);
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    const int xi = xsub + XS * t;
+                    const int i = i0 + xi;
+                    const int v = i + nx * (j + ny * k);
+                    const int o = row + (xi + 1) * LPC + lc;
+                    const int co = crow + xi + 1;
+                    const float4 cv = cc[2 * co];   // (cx, cy, cz, dre)
+                    const float cxm = cc[2 * (co - 1)].x, cym = cc[2 * (co - HX)].y;
+                    const P xc = pc[o];
+                    const P xw = pc[o - LPC], xe = pc[o + LPC], xs = pc[o - HX * LPC], xn = pc[o + HX * LPC];
+                    const P xu = pn[o];
+                    P a;
+#pragma unroll
+                    for (int u = 0; u < CPL; ++u) {
+                        T r = escale(cv.w, xc.e[u]);
+                        if constexpr (Elem<T>::cplx) r = eadd(r, emul_i(op.w, xc.e[u]));
+                        r = esub(r, escale(cxm, xw.e[u]));
+                        r = esub(r, escale(cv.x, xe.e[u]));
+                        r = esub(r, escale(cym, xs.e[u]));
+                        r = esub(r, escale(cv.y, xn.e[u]));
+                        r = esub(r, escale(czd[t], xd[t].e[u]));
+                        r = esub(r, escale(cv.z, xu.e[u]));
+                        a.e[u] = r;
+                        pq[u] = eadd(pq[u], emul(xc.e[u], r));
+                    }
+                    *reinterpret_cast<P*>(q + (int64_t)v * kp + cb) = a;
+                    xd[t] = xc;
+                    czd[t] = cv.z;
+                }
+            }
+            failed = __syncthreads_or(!ok);  // also: plane k's slot is free for plane k + 3
+            if (!failed && k + 2 <= z1) refill(k + 2);
         }
         if (failed) break;
         // this item's per-lane sums into the CTA's column accumulators, in a fixed order
