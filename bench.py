@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--random-data", action="store_true",
+                    help="draw the data M at random instead of synthesizing it with the forward model (no solve "
+                         "of every physical source before the timed steps; for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-batch8", action="store_true",
@@ -174,8 +177,9 @@ def ncu_traffic(kernel_key, workload):
 
 
 # ---------------------------------------------------------------- our arm
-def setup_problem(D, ctx, wl, inp, prec, rtol, log):
-    """Synthesize D and the data M with the library itself, then set the sampling."""
+def setup_problem(D, ctx, wl, inp, prec, rtol, log, random_data=False):
+    """Synthesize D and the data M with the library itself (or draw M at random), then set
+    the sampling."""
     D.dot_set_grid(ctx, wl.nx, wl.ny, wl.nz, wl.h, wl.bc)
     D.dot_set_omega(ctx, wl.omega_nu)
     D.dot_set_diffusion(ctx, np.full(wl.n, 1.0 / 30.0))
@@ -185,11 +189,17 @@ def setup_problem(D, ctx, wl, inp, prec, rtol, log):
     D.dot_set_diffusion(ctx, Dfield)
     D.dot_set_sources(ctx, inp.B)
     D.dot_set_detectors(ctx, inp.C)
-    t0 = time.perf_counter()
-    D.dot_set_solver(ctx, D.PREC_MIXED, 1e-10, 0)
-    Mclean, _ = D.dot_forward_model(ctx, wl.ns, wl.nd, wl.omega_nu != 0.0)
-    log(f"data synthesis ({wl.ns} source columns): {time.perf_counter() - t0:.1f} s")
-    M = synth.add_noise(Mclean, inp)
+    if random_data:
+        rng = np.random.default_rng(5)
+        M = 1e-6 * rng.standard_normal((wl.nd, wl.ns))
+        if wl.omega_nu:
+            M = M + 1e-6j * rng.standard_normal((wl.nd, wl.ns))
+    else:
+        t0 = time.perf_counter()
+        D.dot_set_solver(ctx, D.PREC_MIXED, 1e-10, 0)
+        Mclean, _ = D.dot_forward_model(ctx, wl.ns, wl.nd, wl.omega_nu != 0.0)
+        log(f"data synthesis ({wl.ns} source columns): {time.perf_counter() - t0:.1f} s")
+        M = synth.add_noise(Mclean, inp)
     D.dot_set_data(ctx, M)
     D.dot_set_sampling(ctx, inp.W, inp.V)
     D.dot_set_solver(ctx, D.PREC_MIXED if prec == "mixed" else D.PREC_FP64, rtol, 0)
@@ -222,7 +232,7 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     ctx = D.dot_create(local)
     D.dot_set_stream(ctx, stream.cuda_stream)
-    Dfield, M = setup_problem(D, ctx, wl, inp, args.precision, args.rtol, log)
+    Dfield, M = setup_problem(D, ctx, wl, inp, args.precision, args.rtol, log, args.random_data)
     D.dot_set_launch_options(ctx, True, args.autotune)
     D.dot_set_stencil_path(ctx, 2 if args.stencil_path is None else args.stencil_path)
     ps = p_sequence(inp, args.warmup + args.steps)
@@ -303,8 +313,9 @@ def run_ours(args):
            "scaling": "weak", "vs_baseline": None,
            "dtype": "c64+f64" if args.precision == "mixed" and wl.omega_nu else
                     ("f32+f64" if args.precision == "mixed" else ("c128" if wl.omega_nu else "f64")),
-           "data": "synthetic (seeded PaLS phantom, Gaussian sources/detectors, data from the FP64-refined "
-                   "forward model + 1% noise)",
+           "data": ("synthetic (seeded PaLS phantom, Gaussian sources/detectors, random data)" if args.random_data
+                    else "synthetic (seeded PaLS phantom, Gaussian sources/detectors, data from the FP64-refined "
+                         "forward model + 1% noise)"),
            "config": {"workload": args.workload, "grid": [wl.nx, wl.ny, wl.nz], "n_voxels": wl.n, "h_cm": wl.h,
                       "omega_over_nu": wl.omega_nu, "ns": wl.ns, "nd": wl.nd, "ls": wl.ls, "ld": wl.ld,
                       "m0": wl.m0, "n_params": wl.np_, "precision": args.precision, "rtol": args.rtol,

@@ -100,6 +100,11 @@ WORKLOADS = {
                                       sampling="gaussian", rtol=1e-10, seed_index=3),
     "dot128x128x128": Workload("dot128x128x128", 128, 128, 128, 0.0625, 0.0, (16, 32), (16, 32),
                                32, 32, 1000, sampling="gaussian", rtol=1e-10, seed_index=4),
+    # the 1M-cell frequency-domain workload with half the columns (16 + 16): the same
+    # kernels in about 7 GB of device memory, for profiler captures of many passes
+    "dot128x128x64_w100MHz_k32": Workload("dot128x128x64_w100MHz_k32", 128, 128, 64, 0.0625, OMEGA_NU_100MHZ,
+                                          (16, 16), (16, 16), 16, 16, 125,
+                                          sampling="gaussian", rtol=1e-10, seed_index=3),
 }
 
 
