@@ -502,7 +502,34 @@ def cpu_baseline(wl, inp, log, Dfield=None):
             "full_evaluation": {"value": 1.0 / per_full, "unit": UNIT, "columns": wl.ns + wl.nd,
                                 "seconds": round(per_full, 1),
                                 "what": "the oracle's own definition: every physical source and detector solved"},
+            "timed_whole": oracle_whole("dot32x32x16", log),
             "host_cores_available": os.cpu_count()}
+
+
+def oracle_whole(name, log):
+    """One whole oracle evaluation (its definition: PaLS, assembly, every physical source and
+    detector solved, misfit, Jacobian tensor, gradient) timed end to end on a small workload,
+    beside the projections above.  The data come from the oracle's forward model first
+    (not timed)."""
+    from oracle import dot_oracle as orc
+    wl = synth.WORKLOADS[name]
+    inp = synth.draw(wl)
+    X = orc.cell_centres(wl.nx, wl.ny, wl.nz, wl.h)
+    kw = dict(mu_in=synth.MU_IN, mu_out=synth.MU_OUT, c=wl.cutoff, eps=wl.eps, gamma=wl.gamma)
+    mu_true = orc.pals_mu(inp.p_true, X, **kw)
+    Dfield = synth.diffusion_from_mua(mu_true)
+    Bd = orc.dense_of_csc(wl.n, inp.B)
+    Cd = orc.dense_of_csc(wl.n, inp.C)
+    A = orc.assemble(Dfield, mu_true, wl.nx, wl.ny, wl.nz, wl.h, wl.bc, wl.omega_nu)
+    M = synth.add_noise(Cd.T @ orc.solve(A, Bd), inp)
+    t0 = time.perf_counter()
+    mu = orc.pals_mu(inp.p0, X, **kw)
+    dmu = orc.pals_dmu_dp(inp.p0, X, **kw)
+    out = orc.evaluate(Dfield, mu, (wl.nx, wl.ny, wl.nz, wl.h), wl.bc, wl.omega_nu, Bd, Cd, M, inp.W, inp.V, dmu=dmu)
+    t = time.perf_counter() - t0
+    log(f"oracle whole evaluation of {name}: {t:.2f} s, f = {out['f']:.6e}")
+    return {"workload": name, "seconds": round(t, 3), "n_voxels": wl.n, "columns_solved": wl.ns + wl.nd,
+            "solver": "sparse LU (the oracle's choice below 2e5 unknowns)"}
 
 
 def run_reference(args):

@@ -1213,21 +1213,23 @@ int dot_optimized_sampling(dot_ctx* c, int qs, int qd, int maxit, double tol, in
     release(Wi);
     release(Vi);
     if (rc != DOT_OK) return rc;
-    DevBuf K, L, G, VW;
+    DevBuf K, L, G, GP, VW;
     const int nmax = std::max(nd, ns);
     rc = ensure(K, (size_t)ns * npar * qd * esz64(c));
     if (rc == DOT_OK) rc = ensure(L, (size_t)nd * npar * qs * esz64(c));
     if (rc == DOT_OK) rc = ensure(G, (size_t)nmax * nmax * 8);
+    if (rc == DOT_OK) rc = ensure(GP, (size_t)kGramPartDoubles * 8);
     if (rc == DOT_OK) rc = ensure(VW, (size_t)std::max(nd * qd, ns * qs) * 8);
     std::vector<double> What, Vhat;
     int sw = 0;
     double obj = 0.0;
     if (rc == DOT_OK)
         rc = optimize_from_tensor(cx_, c->J.p, nd, ns, npar, qs, qd, maxit, tol, K.p, L.p, G.as<double>(),
-                                  VW.as<double>(), c->s, What, Vhat, &sw, &obj);
+                                  GP.as<double>(), VW.as<double>(), c->s, What, Vhat, &sw, &obj);
     release(K);
     release(L);
     release(G);
+    release(GP);
     release(VW);
     if (rc != DOT_OK) return rc;
     complement(ns, qs, What, ls - qs, Ytil, W);

@@ -183,8 +183,12 @@ cudaError_t pals_chain_jp(bool cplx, const double* p, int m0, double gamma, int 
 // ---- optimized sources and detectors (optimize.cu)
 int symmetric_eigen(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& Q);
 void complement(int n, int q, const std::vector<double>& What, int m, const double* Ytil, double* out);
+// Chunks of the long dimension of the Gram products and the scratch for their partial
+// sums (dGpart: kGramPartDoubles doubles).
+constexpr int kGramChunks = 64;
+constexpr int64_t kGramPartDoubles = (int64_t)1 << 18;
 int optimize_from_tensor(bool cplx, const void* Jd, int nd, int ns, int npar, int qs, int qd, int maxit, double tol,
-                         void* scratch_K, void* scratch_L, double* dG, double* dVW, cudaStream_t s,
+                         void* scratch_K, void* scratch_L, double* dG, double* dGpart, double* dVW, cudaStream_t s,
                          std::vector<double>& What, std::vector<double>& Vhat, int* sweeps, double* objective);
 
 }  // namespace dotk

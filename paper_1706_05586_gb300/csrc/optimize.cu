@@ -24,21 +24,25 @@
 namespace dotk {
 
 // ------------------------------------------------------------------ device
-// G[a, b] = Re sum_m X[a + ldx m] conj(X[b + ldx m]) for a, b < n, m < M (16 x 16 tiles).
+// Partial Gram sums over one chunk of m: G_s[a, b] = Re sum_{m in chunk s} X[a + ldx m]
+// conj(X[b + ldx m]) for a, b < n (16 x 16 tiles; blockIdx.z = chunk s of length mchunk).
 template <typename T>
-__global__ void k_gram(const T* __restrict__ X, int n, int64_t M, int64_t ldx, double* __restrict__ G) {
+__global__ void k_gram(const T* __restrict__ X, int n, int64_t M, int64_t ldx, int64_t mchunk,
+                       double* __restrict__ G) {
     __shared__ double2 sa[16][17];
     __shared__ double2 sb[16][17];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int a = blockIdx.x * 16 + tx, b = blockIdx.y * 16 + ty;
+    const int64_t mb = (int64_t)blockIdx.z * mchunk, me = M < mb + mchunk ? M : mb + mchunk;
+    G += (size_t)blockIdx.z * n * n;
     double acc = 0.0;
-    for (int64_t m0 = 0; m0 < M; m0 += 16) {
+    for (int64_t m0 = mb; m0 < me; m0 += 16) {
         // load X[blockIdx.x*16 + r, m0 + c] and X[blockIdx.y*16 + r, m0 + c]
         const int r = tx, c = ty;
         const int64_t m = m0 + c;
         const int ra = blockIdx.x * 16 + r, rb = blockIdx.y * 16 + r;
-        sa[c][r] = (ra < n && m < M) ? ewide(X[ra + ldx * m]) : make_double2(0.0, 0.0);
-        sb[c][r] = (rb < n && m < M) ? ewide(X[rb + ldx * m]) : make_double2(0.0, 0.0);
+        sa[c][r] = (ra < n && m < me) ? ewide(X[ra + ldx * m]) : make_double2(0.0, 0.0);
+        sb[c][r] = (rb < n && m < me) ? ewide(X[rb + ldx * m]) : make_double2(0.0, 0.0);
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
@@ -100,12 +104,37 @@ __global__ void k_contract_src(const T* __restrict__ J, int nd, int ns, int npar
     }
 }
 
-static cudaError_t gram(bool cplx, const void* X, int n, int64_t M, int64_t ldx, double* G, cudaStream_t s) {
-    dim3 blk(16, 16), grd((n + 15) / 16, (n + 15) / 16);
+// G = sum of the chunk partials in chunk order (deterministic).
+__global__ void k_gram_sum(const double* __restrict__ part, int chunks, int64_t nn, double* __restrict__ G) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < chunks; ++c) acc += part[(size_t)c * nn + t];
+        G[t] = acc;
+    }
+}
+
+// Gram matrix of the n rows of X.  Small n gives few 16 x 16 tiles, so the long
+// dimension M is split into chunks (about 608 blocks in all, at most kGramChunks) whose
+// partial sums go to `part` and are added in chunk order.
+static cudaError_t gram(bool cplx, const void* X, int n, int64_t M, int64_t ldx, double* G, double* part,
+                        cudaStream_t s) {
+    const int tn = (n + 15) / 16;
+    int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(kGramChunks, 608 / ((int64_t)tn * tn)));
+    chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, M / 256));
+    int64_t mchunk = (M + chunks - 1) / chunks;
+    mchunk = (mchunk + 15) / 16 * 16;
+    chunks = std::max<int64_t>(1, (M + mchunk - 1) / mchunk);
+    if ((int64_t)n * n * chunks > kGramPartDoubles) chunks = 1, mchunk = M;
+    double* dst = chunks > 1 ? part : G;
+    dim3 blk(16, 16), grd(tn, tn, (unsigned)chunks);
     if (cplx)
-        k_gram<double2><<<grd, blk, 0, s>>>((const double2*)X, n, M, ldx, G);
+        k_gram<double2><<<grd, blk, 0, s>>>((const double2*)X, n, M, ldx, mchunk, dst);
     else
-        k_gram<double><<<grd, blk, 0, s>>>((const double*)X, n, M, ldx, G);
+        k_gram<double><<<grd, blk, 0, s>>>((const double*)X, n, M, ldx, mchunk, dst);
+    if (chunks > 1) {
+        const int64_t nn = (int64_t)n * n;
+        k_gram_sum<<<(unsigned)std::min<int64_t>((nn + 255) / 256, 1024), 256, 0, s>>>(part, (int)chunks, nn, G);
+    }
     return cudaGetLastError();
 }
 
@@ -278,7 +307,7 @@ void complement(int n, int q, const std::vector<double>& What, int m, const doub
 }
 
 int optimize_from_tensor(bool cplx, const void* Jd, int nd, int ns, int npar, int qs, int qd, int maxit, double tol,
-                         void* scratch_K, void* scratch_L, double* dG, double* dVW, cudaStream_t s,
+                         void* scratch_K, void* scratch_L, double* dG, double* dGpart, double* dVW, cudaStream_t s,
                          std::vector<double>& What, std::vector<double>& Vhat, int* sweeps, double* objective) {
     const size_t es = cplx ? 16 : 8;
     (void)es;
@@ -307,7 +336,7 @@ int optimize_from_tensor(bool cplx, const void* Jd, int nd, int ns, int npar, in
         if (e_ != cudaSuccess) return record_error(DOT_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
     } while (0)
     // step (1): V~ from J~ = [J_{:,1,:} ... J_{:,ns,:}], rows m, columns j + ns k, stride nd
-    OPT_CK(gram(cplx, Jd, nd, (int64_t)ns * npar, nd, dG, s));
+    OPT_CK(gram(cplx, Jd, nd, (int64_t)ns * npar, nd, dG, dGpart, s));
     OPT_TRY(fetch(nd));
     OPT_TRY(leading_vectors(nd, G, qd, Vhat));
     std::vector<double> Wold, Vold;
@@ -316,14 +345,14 @@ int optimize_from_tensor(bool cplx, const void* Jd, int nd, int ns, int npar, in
         // step (2): W~ from K~ = [K_1 ... K_qd]
         OPT_TRY(upload(Vhat));
         OPT_CK(contract_det(cplx, Jd, nd, ns, npar, dVW, qd, scratch_K, s));
-        OPT_CK(gram(cplx, scratch_K, ns, (int64_t)npar * qd, ns, dG, s));
+        OPT_CK(gram(cplx, scratch_K, ns, (int64_t)npar * qd, ns, dG, dGpart, s));
         OPT_TRY(fetch(ns));
         std::vector<double> Wn;
         OPT_TRY(leading_vectors(ns, G, qs, Wn));
         // step (3): V~ from L~ = [L_1 ... L_qs]
         OPT_TRY(upload(Wn));
         OPT_CK(contract_src(cplx, Jd, nd, ns, npar, dVW, qs, scratch_L, s));
-        OPT_CK(gram(cplx, scratch_L, nd, (int64_t)npar * qs, nd, dG, s));
+        OPT_CK(gram(cplx, scratch_L, nd, (int64_t)npar * qs, nd, dG, dGpart, s));
         OPT_TRY(fetch(nd));
         std::vector<double> Vn;
         OPT_TRY(leading_vectors(nd, G, qd, Vn));
@@ -338,7 +367,7 @@ int optimize_from_tensor(bool cplx, const void* Jd, int nd, int ns, int npar, in
     // objective ||(W^T (x) V^T) J||_F^2 = ||W^T K~||_F^2 with K~ from the final V^
     OPT_TRY(upload(Vhat));
     OPT_CK(contract_det(cplx, Jd, nd, ns, npar, dVW, qd, scratch_K, s));
-    OPT_CK(gram(cplx, scratch_K, ns, (int64_t)npar * qd, ns, dG, s));
+    OPT_CK(gram(cplx, scratch_K, ns, (int64_t)npar * qd, ns, dG, dGpart, s));
     OPT_TRY(fetch(ns));
     double obj = 0.0;
     for (int l = 0; l < qs; ++l)
