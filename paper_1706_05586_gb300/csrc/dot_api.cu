@@ -206,6 +206,7 @@ struct dot_ctx {
 
     bool post_valid = false;
     DevBuf Tm, S, Rs, f, gmu, gp, J, tmp;
+    DevBuf bcount, boffs, bcell, bdval;  // band lists of dmu/dp per RBF (J_p and the Jacobian tensor)
 
     dot_stats stats{};
 
@@ -413,8 +414,14 @@ int apply_tuning(dot_ctx* c, SolveRun& r, const Tuning& t) {
     if (t.tma && !r.tma_ready) {
         CK(tma_stencil_prepare(r.inner, r.ring, c->cf32.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma));
         r.tma.fused = false;
-        if (c->stencil_mode == 2 && dpq_eligible(r.inner, c->nx, c->ny, r.kp))
-            CK(dpq_prepare(r.inner, r.ring, c->ri.p, c->cf8.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma));
+        // the fused kernel is an option on top of the TMA stencil: if its tensor maps or
+        // launch shape cannot be set up, the solve runs the separate direction pass
+        if (c->stencil_mode == 2 && dpq_eligible(r.inner, c->nx, c->ny, r.kp) &&
+            dpq_prepare(r.inner, r.ring, c->ri.p, c->cf8.p, c->nx, c->ny, c->nz, r.kp, c->num_sms, &r.tma) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            r.tma.fused = false;
+        }
         r.tma_ready = true;
     }
     r.fused = t.tma && t.fused && r.tma.fused;
@@ -755,6 +762,28 @@ int ensure_post(dot_ctx* c) {
     return DOT_OK;
 }
 
+// Band lists of dmu/dp at the current PaLS parameters (ensure_coefficients has run): count
+// per RBF, exclusive offsets on the host, then the cells and their five derivatives.
+int build_band_lists(dot_ctx* c) {
+    const int m0 = c->m0;
+    TRY(ensure(c->bcount, (size_t)m0 * 8));
+    TRY(ensure(c->boffs, (size_t)(m0 + 1) * 8));
+    CK(pals_band_count(c->p.as<double>(), m0, c->gamma, c->nx, c->ny, c->nz, c->h, c->wdmu.as<double>(),
+                       c->bcount.as<int64_t>(), c->s));
+    std::vector<int64_t> cnt(m0), offs(m0 + 1, 0);
+    CK(cudaMemcpyAsync(cnt.data(), c->bcount.p, (size_t)m0 * 8, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    for (int j = 0; j < m0; ++j) offs[j + 1] = offs[j] + cnt[j];
+    CK(cudaMemcpyAsync(c->boffs.p, offs.data(), (size_t)(m0 + 1) * 8, cudaMemcpyHostToDevice, c->s));
+    TRY(ensure(c->bcell, (size_t)std::max<int64_t>(offs[m0], 1) * 8));
+    TRY(ensure(c->bdval, (size_t)std::max<int64_t>(offs[m0], 1) * 40));
+    CK(pals_band_fill(c->p.as<double>(), m0, c->gamma, c->nx, c->ny, c->nz, c->h, c->wdmu.as<double>(),
+                      c->boffs.as<int64_t>(), c->bcell.as<int64_t>(), c->bdval.as<double>(), c->s));
+    CK(cudaStreamSynchronize(c->s));  // the host offsets must outlive the copy
+    count(c, 2);
+    return DOT_OK;
+}
+
 // CSC (colptr, rows) -> CSR by voxel with the column index, on the host.
 void csc_to_csr(int64_t n, int ncol, const int64_t* colptr, const int32_t* rows, const double* vals,
                 std::vector<int64_t>& rp, std::vector<int32_t>& ci, std::vector<double>& cv) {
@@ -850,7 +879,8 @@ int dot_destroy(dot_ctx* c) {
     DevBuf* bufs[] = {&c->D, &c->mu, &c->phi, &c->wdmu, &c->p, &c->cf64, &c->dinv64, &c->cf32, &c->dinv32, &c->cf8, &c->rpB, &c->ciB, &c->vB, &c->rpC,
                       &c->ciC, &c->vC, &c->cpC, &c->rwC, &c->vCc, &c->W, &c->V, &c->M, &c->MW, &c->P, &c->b64,
                       &c->x64, &c->r64, &c->xi, &c->ri, &c->pi, &c->qi, &c->colbuf, &c->partA, &c->partB, &c->gcount, &c->Tm,
-                      &c->S, &c->Rs, &c->f, &c->gmu, &c->gp, &c->J, &c->tmp};
+                      &c->S, &c->Rs, &c->f, &c->gmu, &c->gp, &c->J, &c->tmp, &c->bcount, &c->boffs, &c->bcell,
+                      &c->bdval};
     for (DevBuf* b : bufs) release(*b);
     for (int t = 0; t < 4; ++t)
         if (c->ev[t]) cudaEventDestroy(c->ev[t]);
@@ -1199,9 +1229,10 @@ int dot_optimized_sampling(dot_ctx* c, int qs, int qd, int maxit, double tol, in
         rc = ensure_fields(c);
     }
     if (rc == DOT_OK) rc = ensure(c->J, (size_t)nd * ns * npar * esz64(c));
+    if (rc == DOT_OK) rc = build_band_lists(c);
     if (rc == DOT_OK) {
-        cudaError_t e = pals_chain_jp(cx_, c->p.as<double>(), c->m0, c->gamma, c->nx, c->ny, c->nz, c->h,
-                                      c->wdmu.as<double>(), c->x64.p, c->kp, ns, nd, c->J.as<double>(), c->s);
+        cudaError_t e = pals_chain_jp(cx_, c->m0, c->boffs.as<int64_t>(), c->bcell.as<int64_t>(),
+                                      c->bdval.as<double>(), c->x64.p, c->kp, ns, nd, c->J.as<double>(), c->s);
         count(c, 1);
         if (e != cudaSuccess) rc = fail(DOT_ECUDA, std::string("jacobian tensor: ") + cudaGetErrorString(e));
     }
@@ -1259,7 +1290,8 @@ int dot_jacobian_p(dot_ctx* c, double* Jp) {
     TRY(ensure_fields(c));
     const size_t cnt = (size_t)c->ls * c->ld * 5 * c->m0;
     TRY(ensure(c->J, cnt * esz64(c)));
-    CK(pals_chain_jp(cplx(c), c->p.as<double>(), c->m0, c->gamma, c->nx, c->ny, c->nz, c->h, c->wdmu.as<double>(),
+    TRY(build_band_lists(c));
+    CK(pals_chain_jp(cplx(c), c->m0, c->boffs.as<int64_t>(), c->bcell.as<int64_t>(), c->bdval.as<double>(),
                      c->x64.p, c->kp, c->ls, c->ld, c->J.as<double>(), c->s));
     CK(cudaMemcpyAsync(Jp, c->J.p, cnt * esz64(c), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));

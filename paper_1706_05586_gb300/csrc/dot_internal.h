@@ -176,9 +176,16 @@ cudaError_t jacobian_mua(bool cplx, const void* X, int64_t n, int kp, int ls, in
                          cudaStream_t s);
 cudaError_t pals_chain_gp(const double* p, int m0, double gamma, int nx, int ny, int nz, double h,
                           const double* wdmu, const double* gmu, double* gp, cudaStream_t s);
-cudaError_t pals_chain_jp(bool cplx, const double* p, int m0, double gamma, int nx, int ny, int nz,
-                          double h, const double* wdmu, const void* X, int kp, int ls, int ld,
-                          double* Jp, cudaStream_t s);
+// Band lists of the PaLS derivative: per RBF the cells of its support where dmu/dp is
+// nonzero, in box order, with the five derivatives.  count: counts[m0]; fill: from the
+// exclusive offsets offs[m0 + 1] into cell[offs[m0]] and dval[5 offs[m0]].
+cudaError_t pals_band_count(const double* p, int m0, double gamma, int nx, int ny, int nz, double h,
+                            const double* wdmu, int64_t* counts, cudaStream_t s);
+cudaError_t pals_band_fill(const double* p, int m0, double gamma, int nx, int ny, int nz, double h,
+                           const double* wdmu, const int64_t* offs, int64_t* cell, double* dval, cudaStream_t s);
+// J_p = J_mu dmu/dp for the block's l_s forward and l_d adjoint columns over the band lists.
+cudaError_t pals_chain_jp(bool cplx, int m0, const int64_t* offs, const int64_t* cell, const double* dval,
+                          const void* X, int kp, int ls, int ld, double* Jp, cudaStream_t s);
 
 // ---- optimized sources and detectors (optimize.cu)
 int symmetric_eigen(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& Q);
@@ -186,7 +193,7 @@ void complement(int n, int q, const std::vector<double>& What, int m, const doub
 // Chunks of the long dimension of the Gram products and the scratch for their partial
 // sums (dGpart: kGramPartDoubles doubles).
 constexpr int kGramChunks = 64;
-constexpr int64_t kGramPartDoubles = (int64_t)1 << 18;
+constexpr int64_t kGramPartDoubles = (int64_t)1 << 22;
 int optimize_from_tensor(bool cplx, const void* Jd, int nd, int ns, int npar, int qs, int qd, int maxit, double tol,
                          void* scratch_K, void* scratch_L, double* dG, double* dGpart, double* dVW, cudaStream_t s,
                          std::vector<double>& What, std::vector<double>& Vhat, int* sweeps, double* objective);

@@ -585,72 +585,130 @@ cudaError_t pals_chain_gp(const double* p, int m0, double gamma, int nx, int ny,
     return cudaGetLastError();
 }
 
-// J_p[(l + ld i), 5j + q] = sum_v J_mu[(l + ld i), v] dmu_v/dp_{j,q}: one block per RBF,
-// threads over Jacobian rows, voxels of the support staged through shared memory.
-template <typename T>
-__global__ void k_chain_jp(const double* __restrict__ p, int m0, double gamma, int nx, int ny, int nz, double h,
-                           const double* __restrict__ wdmu, const T* __restrict__ X, int kp, int ls, int ld,
-                           T* __restrict__ Jp) {
-    constexpr int CH = 64;
-    __shared__ double sd[CH][5];
-    __shared__ int64_t sv[CH];
-    __shared__ int sflag[CH];
+// Band lists: for RBF j, the cells of its support box where the Heaviside derivative is
+// nonzero and the cell lies inside the support, in box order, with their five
+// d mu / d p_{j,q}.  Pass 1 (cell == nullptr) counts them per RBF; pass 2 writes them
+// from offs[j].  One block per RBF; the block keeps the box order by an ordered
+// compaction (warp ballots, then warp offsets in warp order).
+__global__ void k_band(const double* __restrict__ p, int m0, double gamma, int nx, int ny, int nz, double h,
+                       const double* __restrict__ wdmu, int64_t* __restrict__ counts, const int64_t* __restrict__ offs,
+                       int64_t* __restrict__ cell, double* __restrict__ dval) {
+    __shared__ int wtot[32];
+    __shared__ int64_t base;
     const int j = blockIdx.x;
+    if (j >= m0) return;
     const double* pj = p + 5 * j;
-    const int nr = ls * ld;
     const Box b = rbf_box(pj[1], pj[2], pj[3], pj[4], gamma, nx, ny, nz, h);
     const bool nonempty = b.i1 >= b.i0 && b.j1 >= b.j0 && b.k1 >= b.k0;
     const int bx = b.i1 - b.i0 + 1, by = b.j1 - b.j0 + 1, bz = b.k1 - b.k0 + 1;
     const int64_t cnt = nonempty ? (int64_t)bx * by * bz : 0;
-    for (int r0 = 0; r0 < nr; r0 += blockDim.x) {
-        const int row = r0 + threadIdx.x;
-        const int l = row % ld, i = row / ld;
-        T acc[5];
-        for (int q = 0; q < 5; ++q) acc[q] = ezero<T>();
-        for (int64_t t0 = 0; t0 < cnt; t0 += CH) {
-            __syncthreads();
-            for (int u = threadIdx.x; u < CH; u += blockDim.x) {
-                const int64_t t = t0 + u;
-                sflag[u] = 0;
-                if (t < cnt) {
-                    const int ii = b.i0 + (int)(t % bx);
-                    const int jj = b.j0 + (int)((t / bx) % by);
-                    const int kk = b.k0 + (int)(t / ((int64_t)bx * by));
-                    const int64_t v = ii + (int64_t)nx * (jj + (int64_t)ny * kk);
-                    const double wd = wdmu[v];
-                    double d[5];
-                    if (wd != 0.0 && dmu_dp(pj, gamma, (ii + 0.5) * h, (jj + 0.5) * h, (kk + 0.5) * h, wd, d)) {
-                        sflag[u] = 1;
-                        sv[u] = v;
-                        for (int q = 0; q < 5; ++q) sd[u][q] = d[q];
-                    }
-                }
-            }
-            __syncthreads();
-            if (row < nr) {
-                for (int u = 0; u < CH; ++u) {
-                    if (!sflag[u]) continue;
-                    const T* xr = X + sv[u] * kp;
-                    const T jm = escale(-1.0, emul(xr[ls + l], xr[i]));
-                    for (int q = 0; q < 5; ++q) acc[q] = eadd(acc[q], escale(sd[u][q], jm));
-                }
-            }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) base = cell ? offs[j] : 0;
+    __syncthreads();
+    for (int64_t t0 = 0; t0 < cnt; t0 += blockDim.x) {
+        const int64_t t = t0 + threadIdx.x;
+        double d[5];
+        int64_t v = 0;
+        bool on = false;
+        if (t < cnt) {
+            const int ii = b.i0 + (int)(t % bx);
+            const int jj = b.j0 + (int)((t / bx) % by);
+            const int kk = b.k0 + (int)(t / ((int64_t)bx * by));
+            v = ii + (int64_t)nx * (jj + (int64_t)ny * kk);
+            const double wd = wdmu[v];
+            on = wd != 0.0 && dmu_dp(pj, gamma, (ii + 0.5) * h, (jj + 0.5) * h, (kk + 0.5) * h, wd, d);
         }
-        if (row < nr)
-            for (int q = 0; q < 5; ++q) Jp[row + (int64_t)nr * (5 * j + q)] = acc[q];
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) wtot[warp] = __popc(bal);
+        __syncthreads();
+        int64_t before = base;
+        for (int w = 0; w < warp; ++w) before += wtot[w];
+        if (on && cell) {
+            const int64_t at = before + __popc(bal & ((1u << lane) - 1u));
+            cell[at] = v;
+            for (int q = 0; q < 5; ++q) dval[5 * at + q] = d[q];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 0; w < nw; ++w) base += wtot[w];
+        __syncthreads();
     }
+    if (!cell && threadIdx.x == 0) counts[j] = base;
 }
 
-cudaError_t pals_chain_jp(bool cplx, const double* p, int m0, double gamma, int nx, int ny, int nz, double h,
-                          const double* wdmu, const void* X, int kp, int ls, int ld, double* Jp, cudaStream_t s) {
-    if (m0 <= 0) return cudaSuccess;
+// J_p[(l + ld i), 5j + q] = sum_v J_mu[(l + ld i), v] dmu_v/dp_{j,q} over RBF j's band
+// list: block (j, g) takes rows g * 256 * RPT ..., each thread RPT rows spaced 256 apart
+// (consecutive rows across a warp: consecutive detectors l of one source i, so the
+// adjoint-field loads coalesce); band entries staged through shared memory in chunks.
+template <typename T, int RPT>
+__global__ void __launch_bounds__(256) k_chain_jp(const T* __restrict__ X, int kp, int ls, int ld,
+                                                  const int64_t* __restrict__ offs, const int64_t* __restrict__ cell,
+                                                  const double* __restrict__ dval, T* __restrict__ Jp) {
+    constexpr int CH = 64;
+    __shared__ double sd[CH][5];
+    __shared__ int64_t sv[CH];
+    const int j = blockIdx.x;
     const int nr = ls * ld;
-    const int th = nr >= 256 ? 256 : ((nr + 31) / 32) * 32;
+    const int64_t e0 = offs[j], e1 = offs[j + 1];
+    int row[RPT], l[RPT], i[RPT];
+    T acc[RPT][5];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        row[u] = (blockIdx.y * RPT + u) * 256 + threadIdx.x;
+        l[u] = row[u] % ld;
+        i[u] = row[u] / ld;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc[u][q] = ezero<T>();
+    }
+    for (int64_t t0 = e0; t0 < e1; t0 += CH) {
+        const int m = (int)(e1 - t0 < CH ? e1 - t0 : CH);
+        __syncthreads();
+        for (int u = threadIdx.x; u < m; u += blockDim.x) {
+            sv[u] = cell[t0 + u];
+            for (int q = 0; q < 5; ++q) sd[u][q] = dval[5 * (t0 + u) + q];
+        }
+        __syncthreads();
+        for (int e = 0; e < m; ++e) {
+            const T* xr = X + sv[e] * kp;
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                if (row[u] >= nr) continue;
+                const T jm = escale(-1.0, emul(xr[ls + l[u]], xr[i[u]]));
+#pragma unroll
+                for (int q = 0; q < 5; ++q) acc[u][q] = eadd(acc[u][q], escale(sd[e][q], jm));
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < RPT; ++u)
+        if (row[u] < nr)
+            for (int q = 0; q < 5; ++q) Jp[row[u] + (int64_t)nr * (5 * j + q)] = acc[u][q];
+}
+
+cudaError_t pals_band_count(const double* p, int m0, double gamma, int nx, int ny, int nz, double h,
+                            const double* wdmu, int64_t* counts, cudaStream_t s) {
+    if (m0 <= 0) return cudaSuccess;
+    k_band<<<m0, 256, 0, s>>>(p, m0, gamma, nx, ny, nz, h, wdmu, counts, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t pals_band_fill(const double* p, int m0, double gamma, int nx, int ny, int nz, double h,
+                           const double* wdmu, const int64_t* offs, int64_t* cell, double* dval, cudaStream_t s) {
+    if (m0 <= 0) return cudaSuccess;
+    k_band<<<m0, 256, 0, s>>>(p, m0, gamma, nx, ny, nz, h, wdmu, nullptr, offs, cell, dval);
+    return cudaGetLastError();
+}
+
+cudaError_t pals_chain_jp(bool cplx, int m0, const int64_t* offs, const int64_t* cell, const double* dval,
+                          const void* X, int kp, int ls, int ld, double* Jp, cudaStream_t s) {
+    if (m0 <= 0) return cudaSuccess;
+    constexpr int RPT = 4;
+    const int64_t nr = (int64_t)ls * ld;
+    const dim3 grd((unsigned)m0, (unsigned)((nr + 256 * RPT - 1) / (256 * RPT)));
     if (cplx)
-        k_chain_jp<double2><<<m0, th, 0, s>>>(p, m0, gamma, nx, ny, nz, h, wdmu, (const double2*)X, kp, ls, ld,
-                                              (double2*)Jp);
+        k_chain_jp<double2, RPT><<<grd, 256, 0, s>>>((const double2*)X, kp, ls, ld, offs, cell, dval, (double2*)Jp);
     else
-        k_chain_jp<double><<<m0, th, 0, s>>>(p, m0, gamma, nx, ny, nz, h, wdmu, (const double*)X, kp, ls, ld, Jp);
+        k_chain_jp<double, RPT><<<grd, 256, 0, s>>>((const double*)X, kp, ls, ld, offs, cell, dval, Jp);
     return cudaGetLastError();
 }
 

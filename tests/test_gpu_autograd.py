@@ -2,6 +2,8 @@
 against central differences of the library's own misfit, in checkpoint and recompute
 modes, plus a forward/backward at the 128^3 workload (2,097,152 cells, 1,000 RBFs,
 5,000 parameters) checked along a random direction."""
+import time
+
 import numpy as np
 import pytest
 
@@ -61,8 +63,11 @@ def test_backward_after_a_second_forward_uses_its_own_point():
 
 
 def test_autograd_128cubed_against_oracle_and_central_differences():
-    """The 128^3 workload (2,097,152 cells, omega = 0, 1,000 RBFs, 5,000 parameters,
-    32 + 32 columns) through the autograd wrapper in the plain FP64 path:
+    """The 128^3 workload (2,097,152 cells, omega = 0, 1,000 RBFs, 5,000 parameters) sampled
+    as its configuration asks: 24 random + 8 optimized simultaneous sources and detectors
+    from the 512 x 512 physical ones (Algorithm 1 on the full Jacobian tensor at p0,
+    dot_optimized_sampling: a 1,024-column solve and a 512 x 512 x 5,000 tensor), then
+    through the autograd wrapper in the plain FP64 path:
       * the backward pass against the oracle's gradient chain applied to the fields the
         forward pass checkpointed (restriction, the explicit (i, l) sensitivity loops in
         cell chunks, the oracle's PaLS derivative): agreement to rounding, 1e-10
@@ -95,7 +100,19 @@ def test_autograd_128cubed_against_oracle_and_central_differences():
         D.dot_set_sources(h, inp.B)
         D.dot_set_detectors(h, inp.C)
         D.dot_set_data(h, M)
-        D.dot_set_sampling(h, inp.W, inp.V)
+        # 8 optimized + 24 complementary random columns per side (mixed-precision solves)
+        D.dot_set_solver(h, D.PREC_MIXED, 1e-10, 0)
+        q, l = 8, 32
+        Yt = rng.standard_normal((wl.ns, l - q)) / np.sqrt(l - q)
+        Zt = rng.standard_normal((wl.nd, l - q)) / np.sqrt(l - q)
+        t0 = time.perf_counter()
+        W, V, sweeps, obj = D.dot_optimized_sampling(h, q, q, wl.ns, wl.nd, l, l, Yt, Zt)
+        print(f"optimized sampling at 128^3: {time.perf_counter() - t0:.1f} s, {sweeps} sweeps, objective {obj:.3e}")
+        assert np.allclose(W[:, :q].T @ W[:, :q], np.eye(q), atol=1e-10)
+        assert np.allclose(V[:, :q].T @ V[:, :q], np.eye(q), atol=1e-10)
+        assert np.abs(W[:, :q].T @ W[:, q:]).max() < 1e-10 and np.abs(V[:, :q].T @ V[:, q:]).max() < 1e-10
+        assert 1 <= sweeps <= 100 and obj > 0
+        D.dot_set_sampling(h, W, V)
         D.dot_set_solver(h, D.PREC_FP64, 1e-13, 0)
         p = torch.tensor(inp.p0, dtype=torch.float64, device="cuda", requires_grad=True)
         f = misfit(p, h, _consts(wl))
@@ -104,8 +121,8 @@ def test_autograd_128cubed_against_oracle_and_central_differences():
         U, Z = D.dot_get_fields(h, wl.n, wl.ls, wl.ld, False)
         # the oracle's chain on these fields
         C = orc.sparse_of_csc(wl.n, inp.C)
-        CV = C @ inp.V
-        R_s = CV.T @ U - inp.V.T @ M @ inp.W
+        CV = C @ V
+        R_s = CV.T @ U - V.T @ M @ W
         assert abs(f.item() - float(np.sum(R_s ** 2))) <= 1e-10 * f.item()
         r_abs = np.abs(R_s).ravel(order="F")
         g_mu = np.empty(wl.n)

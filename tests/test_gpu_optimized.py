@@ -19,6 +19,12 @@ CASES = {
                                          sampling="gaussian", seed_index=81),
     "cplx_12x12x9": synth.small_workload(12, 12, 9, 0.3, omega_nu=0.4, src_grid=(4, 2), det_grid=(3, 3), ls=5, ld=4,
                                          m0=5, sampling="gaussian", seed_index=82),
+    # 128 x 128 physical sources and detectors: the Gram products of the unfoldings take
+    # the 64 x 64 register-tiled kernel (n >= 128)
+    "real_16x16x8_n128": synth.small_workload(16, 16, 8, 0.3, src_grid=(16, 8), det_grid=(16, 8), ls=4, ld=4,
+                                              m0=4, sampling="gaussian", seed_index=83),
+    "cplx_16x16x8_n128": synth.small_workload(16, 16, 8, 0.3, omega_nu=0.4, src_grid=(8, 16), det_grid=(16, 8),
+                                              ls=4, ld=4, m0=4, sampling="gaussian", seed_index=84),
 }
 
 
