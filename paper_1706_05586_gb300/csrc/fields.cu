@@ -702,13 +702,21 @@ cudaError_t pals_band_fill(const double* p, int m0, double gamma, int nx, int ny
 cudaError_t pals_chain_jp(bool cplx, int m0, const int64_t* offs, const int64_t* cell, const double* dval,
                           const void* X, int kp, int ls, int ld, double* Jp, cudaStream_t s) {
     if (m0 <= 0) return cudaSuccess;
-    constexpr int RPT = 4;
     const int64_t nr = (int64_t)ls * ld;
-    const dim3 grd((unsigned)m0, (unsigned)((nr + 256 * RPT - 1) / (256 * RPT)));
-    if (cplx)
-        k_chain_jp<double2, RPT><<<grd, 256, 0, s>>>((const double2*)X, kp, ls, ld, offs, cell, dval, (double2*)Jp);
-    else
-        k_chain_jp<double, RPT><<<grd, 256, 0, s>>>((const double*)X, kp, ls, ld, offs, cell, dval, Jp);
+    // four rows per thread once there are enough rows to fill the blocks
+    if (nr > 1024) {
+        const dim3 grd((unsigned)m0, (unsigned)((nr + 1023) / 1024));
+        if (cplx)
+            k_chain_jp<double2, 4><<<grd, 256, 0, s>>>((const double2*)X, kp, ls, ld, offs, cell, dval, (double2*)Jp);
+        else
+            k_chain_jp<double, 4><<<grd, 256, 0, s>>>((const double*)X, kp, ls, ld, offs, cell, dval, Jp);
+    } else {
+        const dim3 grd((unsigned)m0, (unsigned)((nr + 255) / 256));
+        if (cplx)
+            k_chain_jp<double2, 1><<<grd, 256, 0, s>>>((const double2*)X, kp, ls, ld, offs, cell, dval, (double2*)Jp);
+        else
+            k_chain_jp<double, 1><<<grd, 256, 0, s>>>((const double*)X, kp, ls, ld, offs, cell, dval, Jp);
+    }
     return cudaGetLastError();
 }
 

@@ -271,14 +271,19 @@ int symmetric_eigen(int n, std::vector<double>& A, std::vector<double>& w, std::
     }
     for (int i = 0; i < n; ++i) d[i] = at(A, i, i);
     for (int i = 0; i + 1 < n; ++i) e[i] = at(A, i + 1, i);
-    // implicit QL on (d, e)
+    // implicit QL on (d, e).  An off-diagonal is negligible next to its two diagonal
+    // neighbours or next to the whole matrix (the largest |d_i| + |e_i|): Gram matrices of
+    // low-rank unfoldings have a cluster of eigenvalues that are zero up to rounding,
+    // whose rounding-level off-diagonals a purely local test would keep sweeping.
+    double tnorm = 0.0;
+    for (int i = 0; i < n; ++i) tnorm = std::max(tnorm, std::fabs(d[i]) + (i + 1 < n ? std::fabs(e[i]) : 0.0));
     for (int l = 0; l < n; ++l) {
         int iter = 0;
         while (true) {
             int m = l;
             for (; m + 1 < n; ++m) {
                 const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
-                if (std::fabs(e[m]) <= 1e-15 * dd) break;
+                if (std::fabs(e[m]) <= 1e-15 * dd || std::fabs(e[m]) <= 1e-16 * tnorm) break;
             }
             if (m == l) break;
             if (++iter > 60) return record_error(DOT_EBREAKDOWN, "symmetric eigensolver did not converge");

@@ -39,3 +39,20 @@ def test_degenerate_and_gram_like():
     U, s, _ = np.linalg.svd(Xr)
     for c in range(3):               # leading eigenvectors = leading left singular vectors
         assert abs(abs(Q[:, -1 - c] @ U[:, c]) - 1.0) < 1e-10
+
+
+@pytest.mark.parametrize("n,rank", [(128, 20), (256, 12), (512, 40)])
+def test_gram_with_many_null_eigenvalues(n, rank):
+    """Gram matrices of low-rank unfoldings (the Jacobian tensors of Algorithm 1): a few
+    eigenvalues spread over decades and n - rank that are zero up to rounding.  The QL
+    sweeps must deflate the rounding-level off-diagonals of that null cluster against
+    the matrix's scale, and the leading eigenpairs must match numpy."""
+    rng = np.random.default_rng(n + rank)
+    X = rng.standard_normal((n, rank)) @ np.diag(10.0 ** -np.linspace(0, 8, rank)) @ rng.standard_normal((rank, 3 * n))
+    G = X @ X.T
+    w, Q = D.dot_symeig(G)
+    ref, V = np.linalg.eigh(G)
+    assert np.allclose(w, ref, rtol=0, atol=1e-12 * ref.max())
+    assert np.allclose(Q.T @ Q, np.eye(n), atol=1e-12)
+    for c in range(4):
+        assert abs(abs(Q[:, -1 - c] @ V[:, -1 - c]) - 1.0) < 1e-10
