@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--optimized", type=int, default=0, metavar="Q",
+                    help="sample Q optimized simultaneous sources and detectors (Algorithm 1 at p0, computed "
+                         "before the timed steps) completed by ls - Q and ld - Q random ones in the "
+                         "complementary subspace; the 128^3 configuration asks for 8")
     ap.add_argument("--random-data", action="store_true",
                     help="draw the data M at random instead of synthesizing it with the forward model (no solve "
                          "of every physical source before the timed steps; for profiler captures)")
@@ -177,7 +181,7 @@ def ncu_traffic(kernel_key, workload):
 
 
 # ---------------------------------------------------------------- our arm
-def setup_problem(D, ctx, wl, inp, prec, rtol, log, random_data=False):
+def setup_problem(D, ctx, wl, inp, prec, rtol, log, random_data=False, optimized=0):
     """Synthesize D and the data M with the library itself (or draw M at random), then set
     the sampling."""
     D.dot_set_grid(ctx, wl.nx, wl.ny, wl.nz, wl.h, wl.bc)
@@ -201,9 +205,21 @@ def setup_problem(D, ctx, wl, inp, prec, rtol, log, random_data=False):
         log(f"data synthesis ({wl.ns} source columns): {time.perf_counter() - t0:.1f} s")
         M = synth.add_noise(Mclean, inp)
     D.dot_set_data(ctx, M)
-    D.dot_set_sampling(ctx, inp.W, inp.V)
+    W, V = inp.W, inp.V
+    if optimized > 0:
+        D.dot_set_pals(ctx, inp.p0, synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
+        D.dot_set_solver(ctx, D.PREC_MIXED, 1e-10, 0)
+        rng = np.random.default_rng(8)
+        q = optimized
+        Yt = rng.standard_normal((wl.ns, wl.ls - q)) / math.sqrt(wl.ls - q)
+        Zt = rng.standard_normal((wl.nd, wl.ld - q)) / math.sqrt(wl.ld - q)
+        t0 = time.perf_counter()
+        W, V, sweeps, _ = D.dot_optimized_sampling(ctx, q, q, wl.ns, wl.nd, wl.ls, wl.ld, Yt, Zt)
+        log(f"optimized sampling ({q} + {wl.ls - q} columns per side, {wl.ns} + {wl.nd} physical): "
+            f"{time.perf_counter() - t0:.1f} s, {sweeps} sweeps")
+    D.dot_set_sampling(ctx, W, V)
     D.dot_set_solver(ctx, D.PREC_MIXED if prec == "mixed" else D.PREC_FP64, rtol, 0)
-    return Dfield, M
+    return Dfield, M, W, V
 
 
 def p_sequence(inp, count, seed=7):
@@ -232,7 +248,8 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     ctx = D.dot_create(local)
     D.dot_set_stream(ctx, stream.cuda_stream)
-    Dfield, M = setup_problem(D, ctx, wl, inp, args.precision, args.rtol, log, args.random_data)
+    Dfield, M, Wsamp, Vsamp = setup_problem(D, ctx, wl, inp, args.precision, args.rtol, log, args.random_data,
+                                            args.optimized)
     D.dot_set_launch_options(ctx, True, args.autotune)
     D.dot_set_stencil_path(ctx, 2 if args.stencil_path is None else args.stencil_path)
     ps = p_sequence(inp, args.warmup + args.steps)
@@ -318,6 +335,7 @@ def run_ours(args):
                          "forward model + 1% noise)"),
            "config": {"workload": args.workload, "grid": [wl.nx, wl.ny, wl.nz], "n_voxels": wl.n, "h_cm": wl.h,
                       "omega_over_nu": wl.omega_nu, "ns": wl.ns, "nd": wl.nd, "ls": wl.ls, "ld": wl.ld,
+                      "optimized_columns_per_side": args.optimized,
                       "m0": wl.m0, "n_params": wl.np_, "precision": args.precision, "rtol": args.rtol,
                       "krylov_iters_per_step": [it[0] for it in iters], "outer_steps": [it[1] for it in iters],
                       "relres_max": max(it[2] for it in iters),
@@ -397,8 +415,8 @@ def run_ours(args):
         hD = pin(Dfield)
         hB = tuple(pin(a) for a in inp.B)
         hC = tuple(pin(a) for a in inp.C)
-        hW = pin(np.asfortranarray(inp.W).ravel(order="F"))
-        hV = pin(np.asfortranarray(inp.V).ravel(order="F"))
+        hW = pin(np.asfortranarray(Wsamp).ravel(order="F"))
+        hV = pin(np.asfortranarray(Vsamp).ravel(order="F"))
         hp = [pin(p) for p in ps]
         nnzB, nnzC = hB[2].size, hC[2].size
         h2d = (wl.n * 8 + wl.np_ * 8 + (wl.n + 1) * 8 + nnzB * 12 + 2 * (wl.n + 1) * 8 + nnzC * 24
