@@ -393,7 +393,7 @@ def run_ours(args):
                                         "S": rel(S_last, ref["S"])},
                               "fp64_same_rtol": errs(fa)}
         at = {"bar": 1e-8, "reference": out["err_vs_fp64"]["reference"], "rtol": None}
-        for r in (1e-11, 1e-12, 1e-13):
+        for r in (1e-11, 1e-12, 3e-13, 1e-13):
             mx = timed_eval(D.PREC_MIXED, r, reps=3)
             e = errs(mx)
             at.setdefault("tried", []).append({"rtol": r, "err": e, "evals_per_s": round(1e3 / mx["ms"], 4)})

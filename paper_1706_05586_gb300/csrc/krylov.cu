@@ -445,8 +445,10 @@ __global__ void __launch_bounds__(1024) k_promote(T64* __restrict__ x64, T* __re
 }
 
 // r64 = b - A x64 in FP64 on the active columns (every column when all != 0).  A
-// refresh round serves every active column at once: one FP64 pass costs the same
-// for one column as for all, and refreshing a column early is always valid.
+// refresh round serves every active column at once, so the columns that asked for it
+// and those close to asking share one round of launches (refreshing a column early is
+// always valid); the pass is bound by the FP64 pipe, 16 fused multiply-adds per complex
+// element.
 // Finaliser (update mode): converged when ||r64|| <= rtol ||b||, stopped when the
 // iteration budget is spent, otherwise the new scale s' = ||r64||, ratio = s / s',
 // and the scaled target tol2 = rtol^2 ||b||^2 / s'^2.

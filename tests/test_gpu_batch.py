@@ -207,3 +207,14 @@ def test_batch_members_match_oracle(problems, prec, rtol, tol):
                            dmu=pb.dmu_of(pb.inp.p0))
         assert abs(f[i] - ref["f"]) <= tol * ref["f"], i
         assert rel(gs[i], ref["g_p"]) <= tol, i
+
+
+def test_stencil_path_rejects_other_modes():
+    h = D.dot_create(0)
+    try:
+        for bad in (-1, 3):
+            with pytest.raises(D.DotError) as e:
+                D.dot_set_stencil_path(h, bad)
+            assert e.value.code == D.DOT_EINVAL
+    finally:
+        D.dot_destroy(h)
