@@ -449,7 +449,12 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
             P* Pn = pn_ring + pslot(z) * PLANE_P;
             const bool own = z >= z0 && z < z1;
             const int64_t zoff = (int64_t)nx * ny * z;
-            for (int cell = warp * XS + xsub; cell < HX * HY; cell += TY * XS) {
+            // the 96 cells of the halo plane a 7-point stencil reads (the four corners are
+            // no cell's neighbour): exactly three passes of 32 cells per warp instruction
+            for (int c = warp * XS + xsub; c < HX * HY - 4; c += TY * XS) {
+                const int hy = c < HX - 2 ? 0 : (c < HX * HY - HX - 2 ? 1 + (c - (HX - 2)) / HX : HY - 1);
+                const int hx = hy == 0 ? c + 1 : (hy == HY - 1 ? c - (HX * HY - HX - 2) + 1 : (c - (HX - 2)) % HX);
+                const int cell = hy * HX + hx;
                 const int o = cell * LPC + lc;
                 const P po = Po[o];
                 P pn = po;
@@ -461,7 +466,6 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
                         if (run[u]) pn.e[u] = eadd(emul(dv, rr.e[u]), emul(bt[u], po.e[u]));
                 }
                 Pn[o] = pn;
-                const int hy = cell / HX, hx = cell - hy * HX;
                 if (own && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
                     const int64_t v = zoff + (int64_t)(i0 + hx - 1) + (int64_t)nx * (j0 + hy - 1);
                     *reinterpret_cast<P*>(p_new + v * kp + cb) = pn;
