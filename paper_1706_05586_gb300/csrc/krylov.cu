@@ -496,6 +496,9 @@ __global__ void __launch_bounds__(1024) k_true_residual(Op<T64> op, const T64* _
     const bool sel = all ? true : (st.active[c] != 0);
     double rr = 0.0;
     if (sel) {
+        // two cells in flight per thread: their neighbour loads overlap, which keeps the
+        // FP64 pipe fed (the sum of |r|^2 keeps its per-thread order)
+#pragma unroll 2
         VOXEL_LOOP(v) {
             const int64_t e = v * kp + c;
             const T64 rv = residual_at(op, b, x64, v, kp, c);

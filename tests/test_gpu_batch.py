@@ -218,3 +218,63 @@ def test_stencil_path_rejects_other_modes():
             assert e.value.code == D.DOT_EINVAL
     finally:
         D.dot_destroy(h)
+
+
+def test_full_size_batch_member_against_oracle():
+    """Two members of the eight-inversion batch workload at full size in one
+    dot_gradient_batch call (96 x 96 x 48 real and 144 x 144 x 72 at 100 MHz, 1,024 x 1,024
+    physical, 40 + 40 columns, mixed precision to 1e-10, autotuned launches): for the
+    complex member the absorption, the FP64 true residual of every column with the
+    oracle's A, and its misfit and PaLS gradient against the oracle's loops applied to
+    its fields (agreement to rounding: 1e-10 relative)."""
+    members = [synth.BATCH8[0], synth.BATCH8[3]]
+    rng = np.random.default_rng(19)
+    kw = dict(mu_in=synth.MU_IN, mu_out=synth.MU_OUT)
+    prep = []
+    for wl in members:
+        inp = synth.draw(wl)
+        X = orc.cell_centres(wl.nx, wl.ny, wl.nz, wl.h)
+        k = dict(kw, c=wl.cutoff, eps=wl.eps, gamma=wl.gamma)
+        Dfield = synth.diffusion_from_mua(orc.pals_mu(inp.p_true, X, **k))
+        M = 1e-6 * rng.standard_normal((wl.nd, wl.ns))
+        if wl.omega_nu:
+            M = M + 1e-6j * rng.standard_normal((wl.nd, wl.ns))
+        prep.append((inp, X, k, Dfield, M))
+    hs = [D.dot_create(0) for _ in members]
+    try:
+        for h, wl, (inp, X, k, Dfield, M) in zip(hs, members, prep):
+            D.dot_set_grid(h, wl.nx, wl.ny, wl.nz, wl.h, wl.bc)
+            D.dot_set_omega(h, wl.omega_nu)
+            D.dot_set_diffusion(h, Dfield)
+            D.dot_set_pals(h, inp.p0, synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
+            D.dot_set_sources(h, inp.B)
+            D.dot_set_detectors(h, inp.C)
+            D.dot_set_data(h, M)
+            D.dot_set_sampling(h, inp.W, inp.V)
+            D.dot_set_solver(h, D.PREC_MIXED, 1e-10, 0)
+            D.dot_set_launch_options(h, True, True)
+        f, gs, rc = D.dot_gradient_batch(hs, [wl.np_ for wl in members])
+        assert rc == D.DOT_OK
+        wl = members[1]
+        U, Z = D.dot_get_fields(hs[1], wl.n, wl.ls, wl.ld, True)
+        mu = D.dot_get_mua(hs[1], wl.n)
+    finally:
+        for h in hs:
+            D.dot_destroy(h)
+    inp, X, k, Dfield, M = prep[1]
+    assert np.max(np.abs(mu - orc.pals_mu(inp.p0, X, **k))) <= 1e-12
+    A = orc.assemble(Dfield, mu, wl.nx, wl.ny, wl.nz, wl.h, wl.bc, wl.omega_nu)
+    B = orc.sparse_of_csc(wl.n, inp.B)
+    C = orc.sparse_of_csc(wl.n, inp.C)
+    for F, Rhs in ((U, B @ inp.W), (Z, C @ inp.V)):
+        res = np.linalg.norm(Rhs - A @ F, axis=0) / np.linalg.norm(Rhs, axis=0)
+        assert np.all(res <= 1.5e-10), res.max()
+    R_s = (C @ inp.V).T @ U - inp.V.T @ M @ inp.W
+    assert abs(f[1] - float(np.sum(np.abs(R_s) ** 2))) <= 1e-10 * f[1]
+    g_mu = np.empty(wl.n)
+    for v0 in range(0, wl.n, 8192):
+        v1 = min(wl.n, v0 + 8192)
+        g_mu[v0:v1] = orc.misfit_gradient(R_s, orc.sampled_jacobian_mua(U[v0:v1], Z[v0:v1], np.eye(wl.ls),
+                                                                        np.eye(wl.ld)))
+    g_ref = orc.pals_dmu_dp(inp.p0, X, **k).T @ g_mu
+    assert np.linalg.norm(gs[1] - g_ref) <= 1e-10 * np.linalg.norm(g_ref)
