@@ -39,6 +39,10 @@ constexpr int THREADS = 32 * TY;     // warp w <-> tile row y = w
 constexpr int CF_BYTES = HX * HY * 16;                    // one plane of packed coefficients
 constexpr int CF_SLOT = (CF_BYTES + 127) / 128 * 128;     // its room in a ring slot
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+// Tile rows of the fused direction + stencil kernel: 8 (two 256-thread blocks per SM).
+// 16 rows (one 512-thread block per SM, 1.41 instead of 1.56 halo cells per cell) was
+// 9% slower at 1M cells x 64 complex64 columns.
+constexpr int kDpqRows = 8;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -320,11 +324,12 @@ __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __gr
 // staging slot is refilled as soon as its plane is converted, so S planes are in
 // flight while a plane is computed.  A lane owns one column (KC = 16 complex or 32
 // real columns: 128-byte rows).
-template <typename T, int KC, int S>
+template <typename T, int KC, int S, int R>
 struct DpqLayout {
-    static constexpr int PLANE = KC * HX * HY;                 // elements of one vector plane
+    static constexpr int HYR = R + 2;                          // halo rows of an R-row tile
+    static constexpr int PLANE = KC * HX * HYR;                // elements of one vector plane
     static constexpr int P_BYTES = PLANE * (int)sizeof(T);
-    static constexpr int C8_BYTES = HX * HY * 32;              // one plane of 32-byte records
+    static constexpr int C8_BYTES = HX * HYR * 32;             // one plane of 32-byte records
     static constexpr int C8_SLOT = (C8_BYTES + 127) / 128 * 128;
     static constexpr int NCF = S + 3;                          // coefficient planes alive
     static constexpr int OFF_PN = 0;                           // 3 converted planes
@@ -346,13 +351,14 @@ struct alignas(16) Pack16 {
     T e[N];
 };
 
-template <typename T, int KC, int S>
-__global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ CUtensorMap tr,
+template <typename T, int KC, int S, int R>
+__global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid_constant__ CUtensorMap tr,
                                                         const __grid_constant__ CUtensorMap tp,
                                                         const __grid_constant__ CUtensorMap tc8, Op<T> op,
                                                         T* __restrict__ p_new, T* __restrict__ q, int kp,
                                                         int zc_len, ColState st, int hslot) {
-    using Ly = DpqLayout<T, KC, S>;
+    using Ly = DpqLayout<T, KC, S, R>;
+    constexpr int HY_ = Ly::HYR;
     using P = Pack16<T>;
     constexpr int CPL = P::N;         // columns per lane
     constexpr int LPC = KC / CPL;     // lanes per cell
@@ -368,12 +374,12 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
     uint64_t* bar = reinterpret_cast<uint64_t*>(base + Ly::OFF_BAR);
     double2* acc = reinterpret_cast<double2*>(base + Ly::OFF_ACC);
     double2* wsum = reinterpret_cast<double2*>(stg);
-    static_assert(TY * 32 * CPL * (int)sizeof(double2) <= 2 * P_BYTES, "per-lane partials fit in staging slot 0");
+    static_assert(R * 32 * CPL * (int)sizeof(double2) <= 2 * P_BYTES, "per-lane partials fit in staging slot 0");
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lc = lane % LPC, xsub = lane / LPC;  // the lane's columns CPL lc .. CPL lc + CPL - 1 of the tile
     const int nx = op.nx, ny = op.ny, nz = op.nz;
-    const int tiles_x = nx / TX, tiles_y = ny / TY, tiles_c = kp / KC;
+    const int tiles_x = nx / TX, tiles_y = ny / R, tiles_c = kp / KC;
     const int zchunks = (nz + zc_len - 1) / zc_len;
     const int nitems = tiles_x * tiles_y * tiles_c * zchunks;
 
@@ -399,7 +405,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
         rem /= tiles_x;
         const int tyi = rem % tiles_y;
         const int zci = rem / tiles_y;
-        const int i0 = txi * TX, j0 = tyi * TY, c0 = cci * KC;
+        const int i0 = txi * TX, j0 = tyi * R, c0 = cci * KC;
         const int z0 = zci * zc_len, z1 = min(z0 + zc_len, nz);
         const int cb = c0 + CPL * lc;   // the lane's first column
         bool run[CPL];
@@ -451,9 +457,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
             const int64_t zoff = (int64_t)nx * ny * z;
             // the 96 cells of the halo plane a 7-point stencil reads (the four corners are
             // no cell's neighbour): exactly three passes of 32 cells per warp instruction
-            for (int c = warp * XS + xsub; c < HX * HY - 4; c += TY * XS) {
-                const int hy = c < HX - 2 ? 0 : (c < HX * HY - HX - 2 ? 1 + (c - (HX - 2)) / HX : HY - 1);
-                const int hx = hy == 0 ? c + 1 : (hy == HY - 1 ? c - (HX * HY - HX - 2) + 1 : (c - (HX - 2)) % HX);
+            for (int c = warp * XS + xsub; c < HX * HY_ - 4; c += R * XS) {
+                const int hy = c < HX - 2 ? 0 : (c < HX * HY_ - HX - 2 ? 1 + (c - (HX - 2)) / HX : HY_ - 1);
+                const int hx = hy == 0 ? c + 1 : (hy == HY_ - 1 ? c - (HX * HY_ - HX - 2) + 1 : (c - (HX - 2)) % HX);
                 const int cell = hy * HX + hx;
                 const int o = cell * LPC + lc;
                 const P po = Po[o];
@@ -466,7 +472,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
                         if (run[u]) pn.e[u] = eadd(emul(dv, rr.e[u]), emul(bt[u], po.e[u]));
                 }
                 Pn[o] = pn;
-                if (own && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
+                if (own && hx >= 1 && hx <= TX && hy >= 1 && hy <= R) {
                     const int64_t v = zoff + (int64_t)(i0 + hx - 1) + (int64_t)nx * (j0 + hy - 1);
                     *reinterpret_cast<P*>(p_new + v * kp + cb) = pn;
                 }
@@ -563,7 +569,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_dpq_tma(const __grid_constant__ 
         if (threadIdx.x < KC) {
             const int t = threadIdx.x, tl = t / CPL, tu = t % CPL;
             double2 sm = make_double2(0.0, 0.0);
-            for (int w = 0; w < TY; ++w)
+            for (int w = 0; w < R; ++w)
                 for (int h = 0; h < XS; ++h) {
                     const double2 pw = wsum[(w * 32 + h * LPC + tl) * CPL + tu];
                     sm.x += pw.x;
@@ -753,23 +759,25 @@ constexpr int kDpqStages = 2;
 
 bool dpq_eligible(ElemKind inner, int nx, int ny, int kp) {
     const int kc = inner == EK_C64 ? 16 : 32;
-    return (inner == EK_C64 || inner == EK_F32) && nx % TX == 0 && ny % TY == 0 && kp % kc == 0 && kp <= 1024 &&
-           encode_fn() != nullptr;
+    return (inner == EK_C64 || inner == EK_F32) && nx % TX == 0 && ny % kDpqRows == 0 && kp % kc == 0 &&
+           kp <= 1024 && encode_fn() != nullptr;
 }
 
 template <typename T, int KC>
 static size_t dpq_smem(int kp) {
-    return 128 + (size_t)DpqLayout<T, KC, kDpqStages>::OFF_ACC + (size_t)kp * sizeof(double2);
+    return 128 + (size_t)DpqLayout<T, KC, kDpqStages, kDpqRows>::OFF_ACC + (size_t)kp * sizeof(double2);
 }
 
 // As tma_configure: the opt-in covers the widest block, whichever context sets it.
 template <typename T, int KC>
 static cudaError_t dpq_configure(size_t smem, int* per_sm) {
     const size_t widest = dpq_smem<T, KC>(1024);
-    cudaError_t e = cudaFuncSetAttribute(k_dpq_tma<T, KC, kDpqStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_dpq_tma<T, KC, kDpqStages, kDpqRows>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(smem > widest ? smem : widest));
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_dpq_tma<T, KC, kDpqStages>, THREADS, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_dpq_tma<T, KC, kDpqStages, kDpqRows>,
+                                                          32 * kDpqRows, smem);
     return e;
 }
 
@@ -783,7 +791,7 @@ cudaError_t dpq_prepare(ElemKind inner, const DirRing& ring, const void* r, cons
     const int kc = cx ? 16 : 32;
     const cuuint64_t dims[4] = {(cuuint64_t)kp, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     const cuuint64_t strides[3] = {(cuuint64_t)kp * es, (cuuint64_t)kp * nx * es, (cuuint64_t)kp * nx * ny * es};
-    const cuuint32_t box[4] = {(cuuint32_t)kc, HX, HY, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)kc, HX, kDpqRows + 2, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUtensorMapDataType dt = cx ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     auto encode = [&](unsigned char* dst, const void* ptr) {
@@ -797,10 +805,10 @@ cudaError_t dpq_prepare(ElemKind inner, const DirRing& ring, const void* r, cons
         if (encode(out->tmap_pf[sl], p) != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
     // 32-byte records {cx, cy, cz, dre, dinv (re, im or value, 0), 0, 0} per cell
-    // viewed as [z][y][8 nx floats]: each plane of the tile arrives as HY rows of 320 bytes
+    // viewed as [z][y][8 nx floats]: each plane of the tile arrives as rows of 320 bytes
     const cuuint64_t cdims[3] = {(cuuint64_t)nx * 8, (cuuint64_t)ny, (cuuint64_t)nz};
     const cuuint64_t cstrides[2] = {(cuuint64_t)nx * 32, (cuuint64_t)nx * ny * 32};
-    const cuuint32_t cbox[3] = {8 * HX, HY, 1};
+    const cuuint32_t cbox[3] = {8 * HX, kDpqRows + 2, 1};
     if (enc(reinterpret_cast<CUtensorMap*>(out->tmap_c8), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(cf8),
             cdims, cstrides, cbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -812,7 +820,7 @@ cudaError_t dpq_prepare(ElemKind inner, const DirRing& ring, const void* r, cons
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     // z-chunk length: whole waves of items against the two halo planes each chunk converts
-    const int tiles = (nx / TX) * (ny / TY) * (kp / kc);
+    const int tiles = (nx / TX) * (ny / kDpqRows) * (kp / kc);
     const int grid_cap = per_sm * num_sms;
     int best = nz;
     double best_cost = 1e300;
@@ -848,7 +856,7 @@ cudaError_t dpq_launch(ElemKind inner, const OpRaw& o, const TmaStencil& t, cons
         op.ny = o.ny;
         op.nz = o.nz;
         float2* pn = static_cast<float2*>(ring.base) + (size_t)slot * ring.slot_elems;
-        k_dpq_tma<float2, 16, kDpqStages><<<t.gridf, THREADS, t.smemf, s>>>(*tr, *tp, *tc, op, pn, (float2*)q, kp,
+        k_dpq_tma<float2, 16, kDpqStages, kDpqRows><<<t.gridf, 32 * kDpqRows, t.smemf, s>>>(*tr, *tp, *tc, op, pn, (float2*)q, kp,
                                                                            t.zcf, st, slot);
     } else if (inner == EK_F32) {
         Op<float> op;
@@ -859,7 +867,7 @@ cudaError_t dpq_launch(ElemKind inner, const OpRaw& o, const TmaStencil& t, cons
         op.ny = o.ny;
         op.nz = o.nz;
         float* pn = static_cast<float*>(ring.base) + (size_t)slot * ring.slot_elems;
-        k_dpq_tma<float, 32, kDpqStages><<<t.gridf, THREADS, t.smemf, s>>>(*tr, *tp, *tc, op, pn, (float*)q, kp,
+        k_dpq_tma<float, 32, kDpqStages, kDpqRows><<<t.gridf, 32 * kDpqRows, t.smemf, s>>>(*tr, *tp, *tc, op, pn, (float*)q, kp,
                                                                           t.zcf, st, slot);
     } else {
         return cudaErrorInvalidValue;
