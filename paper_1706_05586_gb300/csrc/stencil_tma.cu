@@ -57,20 +57,26 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
-// Bounded wait for the given phase parity; false if the budget ran out.
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the given phase parity; false if the budget ran out.  The clock is
+// read only once the first try has failed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget = kWaitCycles) {
     const uint32_t addr = smem_u32(bar);
+    if (mbar_try(addr, parity)) return true;
     const long long t0 = clock64();
     while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (ok) return true;
+        if (mbar_try(addr, parity)) return true;
         if (clock64() - t0 > budget) return false;
     }
 }
@@ -364,9 +370,14 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
     constexpr int LPC = KC / CPL;     // lanes per cell
     constexpr int XS = 32 / LPC;      // cells per warp instruction
     static_assert(LPC == 8, "column tile of 128 bytes");
-    constexpr int PLANE = Ly::PLANE;
     constexpr int P_BYTES = Ly::P_BYTES;
-    constexpr int PLANE_P = PLANE / CPL;  // 16-byte units of one plane
+    constexpr int PLANE_P = Ly::PLANE / CPL;  // 16-byte units of one plane
+    constexpr int NT = TX / XS;               // own cells of a lane in each plane
+    // the cells of a plane that the 7-point stencil reads (the tile and its one-cell
+    // halo in x and y; the four corners are no cell's neighbour), R XS at a time
+    constexpr int NHALO = HX * HY_ - 4;
+    constexpr int NPASS = (NHALO + R * XS - 1) / (R * XS);
+    constexpr bool EXACT = NHALO % (R * XS) == 0;
     unsigned char* base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
     P* pn_ring = reinterpret_cast<P*>(base + Ly::OFF_PN);
     unsigned char* stg = base + Ly::OFF_ST;
@@ -379,9 +390,31 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lc = lane % LPC, xsub = lane / LPC;  // the lane's columns CPL lc .. CPL lc + CPL - 1 of the tile
     const int nx = op.nx, ny = op.ny, nz = op.nz;
+    const int nxy = nx * ny;
+    const int LP = kp / CPL;          // 16-byte units of one cell's columns in global memory
     const int tiles_x = nx / TX, tiles_y = ny / R, tiles_c = kp / KC;
     const int zchunks = (nz + zc_len - 1) / zc_len;
     const int nitems = tiles_x * tiles_y * tiles_c * zchunks;
+
+    // The lane's halo cells, the same in every plane and item: index in the plane of
+    // (HX x HY_) cells, offset from the tile origin in the grid (x + nx y), and a bit
+    // in hown for each that is one of the tile's own cells (hlive: within the plane)
+    int hcell[NPASS], hrel[NPASS];
+    uint32_t hown = 0, hlive = 0;
+#pragma unroll
+    for (int i = 0; i < NPASS; ++i) {
+        const int c = warp * XS + xsub + i * R * XS;
+        const int hy = c < HX - 2 ? 0 : (c < HX * HY_ - HX - 2 ? 1 + (c - (HX - 2)) / HX : HY_ - 1);
+        const int hx = hy == 0 ? c + 1 : (hy == HY_ - 1 ? c - (HX * HY_ - HX - 2) + 1 : (c - (HX - 2)) % HX);
+        const bool live = EXACT || c < NHALO;
+        hcell[i] = live ? hy * HX + hx : 0;
+        hrel[i] = (hx - 1) + nx * (hy - 1);
+        if (live) hlive |= 1u << i;
+        if (live && hx >= 1 && hx <= TX && hy >= 1 && hy <= R) hown |= 1u << i;
+    }
+    // the lane's own cells of its tile row (x = xsub + XS t): offsets from the tile origin
+    const int row = (warp + 1) * HX * LPC;
+    const int crow = (warp + 1) * HX;
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < S; ++b) mbar_init(&bar[b], 1);
@@ -408,6 +441,7 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
         const int i0 = txi * TX, j0 = tyi * R, c0 = cci * KC;
         const int z0 = zci * zc_len, z1 = min(z0 + zc_len, nz);
         const int cb = c0 + CPL * lc;   // the lane's first column
+        const int bcell = i0 + nx * j0; // the tile origin's cell in a plane
         bool run[CPL];
         T bt[CPL];
         bool act = false, anyrun = false;
@@ -421,60 +455,55 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
         }
         // a tile whose columns have all stopped needs neither p_new nor q
         if (!__syncthreads_or(act)) continue;
+        P* const pcol = reinterpret_cast<P*>(p_new + cb);
+        P* const qcol = reinterpret_cast<P*>(q + cb);
 
-        // planes z0-1 .. z1 (z1 is the halo below the chunk; zero-filled past the grid)
-        auto sslot = [&](int z) { return (z - z0 + 1) % S; };
-        auto pslot = [&](int z) { return (z - z0 + 1) % 3; };
-        auto cslot = [&](int z) { return (z - z0 + 1) % Ly::NCF; };
-        auto issue = [&](int z) {
-            const int sl = sslot(z);
+        // Ring positions of plane z: u = z - z0 + 1 counts the chunk's planes from the
+        // halo plane z0 - 1; staging slot u % S, p_new slot u % 3, coefficients u % NCF.
+        auto issue = [&](int z, unsigned u) {
+            const int sl = (int)(u % S);
             unsigned char* d = stg + (size_t)sl * 2 * P_BYTES;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_expect_tx(&bar[sl], 2 * P_BYTES + Ly::C8_BYTES);
             tma_load4(&tr, d, &bar[sl], c0, i0 - 1, j0 - 1, z);
             tma_load4(&tp, d + P_BYTES, &bar[sl], c0, i0 - 1, j0 - 1, z);
-            tma_load3(&tc8, cfr + (size_t)cslot(z) * Ly::C8_SLOT, &bar[sl], 8 * (i0 - 1), j0 - 1, z);
+            tma_load3(&tc8, cfr + (size_t)(u % Ly::NCF) * Ly::C8_SLOT, &bar[sl], 8 * (i0 - 1), j0 - 1, z);
         };
         // (the barrier above also ends the previous item's reads of the partials in slot 0)
         for (int z = z0 - 1; z <= min(z0 - 2 + S, z1); ++z) {
-            if (threadIdx.x == 0) issue(z);
-            pending |= 1u << sslot(z);
+            const unsigned u = (unsigned)(z - z0 + 1);
+            if (threadIdx.x == 0) issue(z, u);
+            pending |= 1u << (u % S);
         }
         // wait for plane z and convert it into its p_new slot (and, for the chunk's own
         // planes, write the tile's cells to the ring slot in global memory); no barrier:
-        // the caller's next barrier ends the reads of the staging slot
-        auto convert = [&](int z) -> bool {
-            const int sl = sslot(z);
-            const bool ok = mbar_wait(&bar[sl], (parity >> sl) & 1u);
-            if (!ok) return false;
+        // the caller's next barrier ends the reads of the staging slot.  Every shared
+        // load of the plane is issued before its first store.
+        auto convert = [&](int z, unsigned u, int ps) -> bool {
+            const int sl = (int)(u % S);
+            if (!mbar_wait(&bar[sl], (parity >> sl) & 1u)) return false;
             parity ^= 1u << sl;
             pending &= ~(1u << sl);
             const P* Rr = reinterpret_cast<const P*>(stg + (size_t)sl * 2 * P_BYTES);
-            const P* Po = reinterpret_cast<const P*>(stg + (size_t)sl * 2 * P_BYTES + P_BYTES);
-            const float4* cw = reinterpret_cast<const float4*>(cfr + (size_t)cslot(z) * Ly::C8_SLOT);
-            P* Pn = pn_ring + pslot(z) * PLANE_P;
+            const P* Po = Rr + PLANE_P;
+            const float4* cw = reinterpret_cast<const float4*>(cfr + (size_t)(u % Ly::NCF) * Ly::C8_SLOT);
+            P* Pn = pn_ring + ps * PLANE_P;
             const bool own = z >= z0 && z < z1;
-            const int64_t zoff = (int64_t)nx * ny * z;
-            // the 96 cells of the halo plane a 7-point stencil reads (the four corners are
-            // no cell's neighbour): exactly three passes of 32 cells per warp instruction
-            for (int c = warp * XS + xsub; c < HX * HY_ - 4; c += R * XS) {
-                const int hy = c < HX - 2 ? 0 : (c < HX * HY_ - HX - 2 ? 1 + (c - (HX - 2)) / HX : HY_ - 1);
-                const int hx = hy == 0 ? c + 1 : (hy == HY_ - 1 ? c - (HX * HY_ - HX - 2) + 1 : (c - (HX - 2)) % HX);
-                const int cell = hy * HX + hx;
-                const int o = cell * LPC + lc;
-                const P po = Po[o];
-                P pn = po;
-                if (anyrun) {
-                    const T dv = dinv_of(cw[2 * cell + 1], (T*)nullptr);
-                    const P rr = Rr[o];
+            P* const pz = pcol + (int64_t)(own ? z : 0) * nxy * LP;
 #pragma unroll
-                    for (int u = 0; u < CPL; ++u)
-                        if (run[u]) pn.e[u] = eadd(emul(dv, rr.e[u]), emul(bt[u], po.e[u]));
-                }
-                Pn[o] = pn;
-                if (own && hx >= 1 && hx <= TX && hy >= 1 && hy <= R) {
-                    const int64_t v = zoff + (int64_t)(i0 + hx - 1) + (int64_t)nx * (j0 + hy - 1);
-                    *reinterpret_cast<P*>(p_new + v * kp + cb) = pn;
+            for (int i = 0; i < NPASS; ++i) {
+                if (EXACT || ((hlive >> i) & 1u)) {
+                    const P po = Po[hcell[i] * LPC + lc];
+                    P pn = po;
+                    if (anyrun) {
+                        const P rr = Rr[hcell[i] * LPC + lc];
+                        const T dv = dinv_of(cw[2 * hcell[i] + 1], (T*)nullptr);
+#pragma unroll
+                        for (int u2 = 0; u2 < CPL; ++u2)
+                            if (run[u2]) pn.e[u2] = eadd(emul(dv, rr.e[u2]), emul(bt[u2], po.e[u2]));
+                    }
+                    Pn[hcell[i] * LPC + lc] = pn;
+                    if (own && ((hown >> i) & 1u)) pz[(int64_t)(bcell + hrel[i]) * LP] = pn;
                 }
             }
             return true;
@@ -482,56 +511,56 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
         // after a barrier that ends every read of plane z's staging slot: refill it
         auto refill = [&](int z) {
             if (z + S <= z1) {
-                if (threadIdx.x == 0) issue(z + S);
-                pending |= 1u << sslot(z + S);
+                const unsigned u = (unsigned)(z + S - z0 + 1);
+                if (threadIdx.x == 0) issue(z + S, u);
+                pending |= 1u << (u % S);
             }
         };
-        // the lane's own cells of its tile row: x = xsub + XS t; their -z neighbours
-        // (p_new and the face coefficient of the plane below) stay in registers from
-        // one plane to the next, so a plane's compute reads only planes k and k + 1
-        constexpr int NT = TX / XS;
-        const int j = j0 + warp;
-        const int row = (warp + 1) * HX * LPC;
-        const int crow = (warp + 1) * HX;
+        // the lane's own cells: their -z neighbours (p_new and the face coefficient of
+        // the plane below) stay in registers from one plane to the next, so a plane's
+        // compute reads only planes k and k + 1
         P xd[NT];
         float czd[NT];
         T pq[CPL];
 #pragma unroll
         for (int u = 0; u < CPL; ++u) pq[u] = ezero<T>();
-        bool ok = convert(z0 - 1);
+        bool ok = convert(z0 - 1, 0u, 0);
         failed = __syncthreads_or(!ok);
         if (!failed) {
             refill(z0 - 1);
-            const P* pl = pn_ring + pslot(z0 - 1) * PLANE_P;
-            const float4* cl = reinterpret_cast<const float4*>(cfr + (size_t)cslot(z0 - 1) * Ly::C8_SLOT);
+            const P* pl = pn_ring;
+            const float4* cl = reinterpret_cast<const float4*>(cfr);
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
                 const int xi = xsub + XS * t;
                 xd[t] = pl[row + (xi + 1) * LPC + lc];
                 czd[t] = cl[2 * (crow + xi + 1)].z;
             }
-            ok = convert(z0);
+            ok = convert(z0, 1u, 1);
             failed = __syncthreads_or(!ok);
         }
         if (!failed) {
             refill(z0);
-            ok = convert(z0 + 1);
+            ok = convert(z0 + 1, 2u, 2);
             failed = __syncthreads_or(!ok);
         }
         if (!failed) refill(z0 + 1);
+        // p_new slots of planes k, k + 1, k + 2 and the coefficient slot of plane k,
+        // advanced by rotation instead of a modulo per plane
+        int ps0 = 1, ps1 = 2, ps2 = 0, cs0 = 1;
         for (int k = z0; k < z1 && !failed; ++k) {
+            const unsigned u2 = (unsigned)(k + 2 - z0 + 1);
             // plane k + 2 goes into the slot plane k - 1 left (its values the stencil needs
             // are the registers xd, czd) while plane k is computed from planes k and k + 1
-            ok = k + 2 > z1 || convert(k + 2);
+            ok = k + 2 > z1 || convert(k + 2, u2, ps2);
             if (ok) {
-                const P* pc = pn_ring + pslot(k) * PLANE_P;
-                const P* pn = pn_ring + pslot(k + 1) * PLANE_P;
-                const float4* cc = reinterpret_cast<const float4*>(cfr + (size_t)cslot(k) * Ly::C8_SLOT);
+                const P* pc = pn_ring + ps0 * PLANE_P;
+                const P* pn = pn_ring + ps1 * PLANE_P;
+                const float4* cc = reinterpret_cast<const float4*>(cfr + (size_t)cs0 * Ly::C8_SLOT);
+                P* const qz = qcol + (int64_t)k * nxy * LP;
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
                     const int xi = xsub + XS * t;
-                    const int i = i0 + xi;
-                    const int v = i + nx * (j + ny * k);
                     const int o = row + (xi + 1) * LPC + lc;
                     const int co = crow + xi + 1;
                     const float4 cv = cc[2 * co];   // (cx, cy, cz, dre)
@@ -553,13 +582,18 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
                         a.e[u] = r;
                         pq[u] = eadd(pq[u], emul(xc.e[u], r));
                     }
-                    *reinterpret_cast<P*>(q + (int64_t)v * kp + cb) = a;
+                    qz[(int64_t)(bcell + xi + nx * warp) * LP] = a;
                     xd[t] = xc;
                     czd[t] = cv.z;
                 }
             }
             failed = __syncthreads_or(!ok);  // also: plane k's slot is free for plane k + 3
             if (!failed && k + 2 <= z1) refill(k + 2);
+            const int pt = ps0;
+            ps0 = ps1;
+            ps1 = ps2;
+            ps2 = pt;
+            cs0 = cs0 + 1 == Ly::NCF ? 0 : cs0 + 1;
         }
         if (failed) break;
         // this item's per-lane sums into the CTA's column accumulators, in a fixed order
