@@ -455,6 +455,10 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
         }
         // a tile whose columns have all stopped needs neither p_new nor q
         if (!__syncthreads_or(act)) continue;
+        bool lane_all = true;
+#pragma unroll
+        for (int u = 0; u < CPL; ++u) lane_all = lane_all && run[u];
+        const bool allrun = __all_sync(0xffffffffu, lane_all);  // warp-uniform: no per-column selects
         P* const pcol = reinterpret_cast<P*>(p_new + cb);
         P* const qcol = reinterpret_cast<P*>(q + cb);
 
@@ -495,7 +499,12 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
                 if (EXACT || ((hlive >> i) & 1u)) {
                     const P po = Po[hcell[i] * LPC + lc];
                     P pn = po;
-                    if (anyrun) {
+                    if (allrun) {
+                        const P rr = Rr[hcell[i] * LPC + lc];
+                        const T dv = dinv_of(cw[2 * hcell[i] + 1], (T*)nullptr);
+#pragma unroll
+                        for (int u2 = 0; u2 < CPL; ++u2) pn.e[u2] = eadd(emul(dv, rr.e[u2]), emul(bt[u2], po.e[u2]));
+                    } else if (anyrun) {
                         const P rr = Rr[hcell[i] * LPC + lc];
                         const T dv = dinv_of(cw[2 * hcell[i] + 1], (T*)nullptr);
 #pragma unroll
@@ -552,8 +561,7 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
             const unsigned u2 = (unsigned)(k + 2 - z0 + 1);
             // plane k + 2 goes into the slot plane k - 1 left (its values the stencil needs
             // are the registers xd, czd) while plane k is computed from planes k and k + 1
-            ok = k + 2 > z1 || convert(k + 2, u2, ps2);
-            if (ok) {
+            {
                 const P* pc = pn_ring + ps0 * PLANE_P;
                 const P* pn = pn_ring + ps1 * PLANE_P;
                 const float4* cc = reinterpret_cast<const float4*>(cfr + (size_t)cs0 * Ly::C8_SLOT);
@@ -587,6 +595,7 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
                     czd[t] = cv.z;
                 }
             }
+            ok = k + 2 > z1 || convert(k + 2, u2, ps2);
             failed = __syncthreads_or(!ok);  // also: plane k's slot is free for plane k + 3
             if (!failed && k + 2 <= z1) refill(k + 2);
             const int pt = ps0;
