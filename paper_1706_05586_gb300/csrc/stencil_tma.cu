@@ -384,8 +384,10 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
     unsigned char* cfr = base + Ly::OFF_CF;
     uint64_t* bar = reinterpret_cast<uint64_t*>(base + Ly::OFF_BAR);
     double2* acc = reinterpret_cast<double2*>(base + Ly::OFF_ACC);
-    double2* wsum = reinterpret_cast<double2*>(stg);
-    static_assert(R * 32 * CPL * (int)sizeof(double2) <= 2 * P_BYTES, "per-lane partials fit in staging slot 0");
+    // per-lane partial sums of an item, in the p_new ring once its planes are consumed
+    // (the staging slots may already hold the next item's first planes)
+    double2* wsum = reinterpret_cast<double2*>(base + Ly::OFF_PN);
+    static_assert(R * 32 * CPL * (int)sizeof(double2) <= 3 * P_BYTES, "per-lane partials fit in the p_new ring");
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lc = lane % LPC, xsub = lane / LPC;  // the lane's columns CPL lc .. CPL lc + CPL - 1 of the tile
@@ -426,11 +428,21 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
     uint32_t parity = 0;    // bit b: parity of the next phase of staging slot b
     uint32_t pending = 0;   // bit b: a copy into staging slot b has been issued and not waited for
     bool failed = false;
+    // Planes are numbered in the order this CTA loads them, across its items: the
+    // plane with number s lands in staging slot s % S, its records in coefficient slot
+    // s % NCF, and it is converted into p_new slot s % 3.  An item's planes z0 - 1 .. z1
+    // are numbers seq0 .. seq0 + z1 - z0 + 1; the first S planes of the next item are
+    // loaded while this one ends, into the staging slots its last planes leave.
+    unsigned seq0 = 0;
+    int npref = 0;          // planes of the current item already loaded by the previous one
 
-    for (int item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
-        // column tiles fastest: the tiles sharing a cell's columns run on neighbouring
-        // CTAs at the same time, so the 256-byte L2 lines their 128-byte rows split are
-        // used by both while resident
+    // tile of a work item: column tiles fastest, so the tiles sharing a cell's columns run
+    // on neighbouring CTAs at the same time and the 256-byte L2 lines their 128-byte rows
+    // split are used by both while resident
+    struct Tile {
+        int i0, j0, c0, z0, z1;
+    };
+    auto tile_of = [&](int item) {
         int rem = item;
         const int cci = rem % tiles_c;
         rem /= tiles_c;
@@ -438,8 +450,28 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
         rem /= tiles_x;
         const int tyi = rem % tiles_y;
         const int zci = rem / tiles_y;
-        const int i0 = txi * TX, j0 = tyi * R, c0 = cci * KC;
-        const int z0 = zci * zc_len, z1 = min(z0 + zc_len, nz);
+        Tile g;
+        g.i0 = txi * TX;
+        g.j0 = tyi * R;
+        g.c0 = cci * KC;
+        g.z0 = zci * zc_len;
+        g.z1 = min(g.z0 + zc_len, nz);
+        return g;
+    };
+    // the copies of plane z of tile g as plane number s (thread 0 only)
+    auto issue = [&](const Tile& g, int z, unsigned s) {
+        const int sl = (int)(s % S);
+        unsigned char* d = stg + (size_t)sl * 2 * P_BYTES;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[sl], 2 * P_BYTES + Ly::C8_BYTES);
+        tma_load4(&tr, d, &bar[sl], g.c0, g.i0 - 1, g.j0 - 1, z);
+        tma_load4(&tp, d + P_BYTES, &bar[sl], g.c0, g.i0 - 1, g.j0 - 1, z);
+        tma_load3(&tc8, cfr + (size_t)(s % Ly::NCF) * Ly::C8_SLOT, &bar[sl], 8 * (g.i0 - 1), g.j0 - 1, z);
+    };
+
+    for (int item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
+        const Tile g = tile_of(item);
+        const int i0 = g.i0, j0 = g.j0, c0 = g.c0, z0 = g.z0, z1 = g.z1;
         const int cb = c0 + CPL * lc;   // the lane's first column
         const int bcell = i0 + nx * j0; // the tile origin's cell in a plane
         bool run[CPL];
@@ -453,44 +485,56 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
             act = act || a;
             anyrun = anyrun || run[u];
         }
-        // a tile whose columns have all stopped needs neither p_new nor q
+        // the CTA's next item, whose first planes are loaded while this one ends when it
+        // has a running column
+        const int nitem = item + (int)gridDim.x;
+        const Tile gn = tile_of(nitem < nitems ? nitem : item);
+        bool nact = false;
+        if (nitem < nitems) {
+#pragma unroll
+            for (int u = 0; u < CPL; ++u) nact = nact || st.active[gn.c0 + CPL * lc + u] != 0;
+        }
+        // a tile whose columns have all stopped needs neither p_new nor q (it was not
+        // prefetched either: npref is 0)
         if (!__syncthreads_or(act)) continue;
+        const bool pf = __syncthreads_or(nact);
         bool lane_all = true;
 #pragma unroll
         for (int u = 0; u < CPL; ++u) lane_all = lane_all && run[u];
         const bool allrun = __all_sync(0xffffffffu, lane_all);  // warp-uniform: no per-column selects
         P* const pcol = reinterpret_cast<P*>(p_new + cb);
         P* const qcol = reinterpret_cast<P*>(q + cb);
+        const unsigned seq_end = seq0 + (unsigned)(z1 - z0 + 2);   // the next item's first plane
+        const unsigned npf = pf ? (unsigned)min(S, gn.z1 - gn.z0 + 2) : 0u;
 
-        // Ring positions of plane z: u = z - z0 + 1 counts the chunk's planes from the
-        // halo plane z0 - 1; staging slot u % S, p_new slot u % 3, coefficients u % NCF.
-        auto issue = [&](int z, unsigned u) {
-            const int sl = (int)(u % S);
-            unsigned char* d = stg + (size_t)sl * 2 * P_BYTES;
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&bar[sl], 2 * P_BYTES + Ly::C8_BYTES);
-            tma_load4(&tr, d, &bar[sl], c0, i0 - 1, j0 - 1, z);
-            tma_load4(&tp, d + P_BYTES, &bar[sl], c0, i0 - 1, j0 - 1, z);
-            tma_load3(&tc8, cfr + (size_t)(u % Ly::NCF) * Ly::C8_SLOT, &bar[sl], 8 * (i0 - 1), j0 - 1, z);
-        };
-        // (the barrier above also ends the previous item's reads of the partials in slot 0)
-        for (int z = z0 - 1; z <= min(z0 - 2 + S, z1); ++z) {
-            const unsigned u = (unsigned)(z - z0 + 1);
-            if (threadIdx.x == 0) issue(z, u);
-            pending |= 1u << (u % S);
+        // this item's first planes that the previous item did not load
+        for (unsigned s = seq0 + (unsigned)npref; s < seq0 + (unsigned)min(S, z1 - z0 + 2); ++s) {
+            if (threadIdx.x == 0) issue(g, z0 - 1 + (int)(s - seq0), s);
+            pending |= 1u << (s % S);
         }
-        // wait for plane z and convert it into its p_new slot (and, for the chunk's own
-        // planes, write the tile's cells to the ring slot in global memory); no barrier:
-        // the caller's next barrier ends the reads of the staging slot.  Every shared
-        // load of the plane is issued before its first store.
-        auto convert = [&](int z, unsigned u, int ps) -> bool {
-            const int sl = (int)(u % S);
+        // after a barrier that ends every read of plane s's staging slot: load plane s + S
+        // into it, of this item or, past its end, of the next
+        auto refill = [&](unsigned s) {
+            const unsigned t = s + S;
+            if (t < seq_end) {
+                if (threadIdx.x == 0) issue(g, z0 - 1 + (int)(t - seq0), t);
+                pending |= 1u << (t % S);
+            } else if (t - seq_end < npf) {
+                if (threadIdx.x == 0) issue(gn, gn.z0 - 1 + (int)(t - seq_end), t);
+                pending |= 1u << (t % S);
+            }
+        };
+        // wait for plane z (number s) and convert it into its p_new slot ps (and, for the
+        // chunk's own planes, write the tile's cells to the ring slot in global memory);
+        // no barrier: the caller's next barrier ends the reads of the staging slot
+        auto convert = [&](int z, unsigned s, int ps) -> bool {
+            const int sl = (int)(s % S);
             if (!mbar_wait(&bar[sl], (parity >> sl) & 1u)) return false;
             parity ^= 1u << sl;
             pending &= ~(1u << sl);
             const P* Rr = reinterpret_cast<const P*>(stg + (size_t)sl * 2 * P_BYTES);
             const P* Po = Rr + PLANE_P;
-            const float4* cw = reinterpret_cast<const float4*>(cfr + (size_t)(u % Ly::NCF) * Ly::C8_SLOT);
+            const float4* cw = reinterpret_cast<const float4*>(cfr + (size_t)(s % Ly::NCF) * Ly::C8_SLOT);
             P* Pn = pn_ring + ps * PLANE_P;
             const bool own = z >= z0 && z < z1;
             P* const pz = pcol + (int64_t)(own ? z : 0) * nxy * LP;
@@ -517,14 +561,6 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
             }
             return true;
         };
-        // after a barrier that ends every read of plane z's staging slot: refill it
-        auto refill = [&](int z) {
-            if (z + S <= z1) {
-                const unsigned u = (unsigned)(z + S - z0 + 1);
-                if (threadIdx.x == 0) issue(z + S, u);
-                pending |= 1u << (u % S);
-            }
-        };
         // the lane's own cells: their -z neighbours (p_new and the face coefficient of
         // the plane below) stay in registers from one plane to the next, so a plane's
         // compute reads only planes k and k + 1
@@ -533,34 +569,34 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
         T pq[CPL];
 #pragma unroll
         for (int u = 0; u < CPL; ++u) pq[u] = ezero<T>();
-        bool ok = convert(z0 - 1, 0u, 0);
+        bool ok = convert(z0 - 1, seq0, (int)(seq0 % 3u));
         failed = __syncthreads_or(!ok);
         if (!failed) {
-            refill(z0 - 1);
-            const P* pl = pn_ring;
-            const float4* cl = reinterpret_cast<const float4*>(cfr);
+            refill(seq0);
+            const P* pl = pn_ring + (seq0 % 3u) * PLANE_P;
+            const float4* cl = reinterpret_cast<const float4*>(cfr + (size_t)(seq0 % Ly::NCF) * Ly::C8_SLOT);
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
                 const int xi = xsub + XS * t;
                 xd[t] = pl[row + (xi + 1) * LPC + lc];
                 czd[t] = cl[2 * (crow + xi + 1)].z;
             }
-            ok = convert(z0, 1u, 1);
+            ok = convert(z0, seq0 + 1, (int)((seq0 + 1) % 3u));
             failed = __syncthreads_or(!ok);
         }
         if (!failed) {
-            refill(z0);
-            ok = convert(z0 + 1, 2u, 2);
+            refill(seq0 + 1);
+            ok = convert(z0 + 1, seq0 + 2, (int)((seq0 + 2) % 3u));
             failed = __syncthreads_or(!ok);
         }
-        if (!failed) refill(z0 + 1);
+        if (!failed) refill(seq0 + 2);
         // p_new slots of planes k, k + 1, k + 2 and the coefficient slot of plane k,
         // advanced by rotation instead of a modulo per plane
-        int ps0 = 1, ps1 = 2, ps2 = 0, cs0 = 1;
+        int ps0 = (int)((seq0 + 1) % 3u), ps1 = (int)((seq0 + 2) % 3u), ps2 = (int)(seq0 % 3u);
+        int cs0 = (int)((seq0 + 1) % Ly::NCF);
         for (int k = z0; k < z1 && !failed; ++k) {
-            const unsigned u2 = (unsigned)(k + 2 - z0 + 1);
-            // plane k + 2 goes into the slot plane k - 1 left (its values the stencil needs
-            // are the registers xd, czd) while plane k is computed from planes k and k + 1
+            // plane k from planes k and k + 1 (and the registers xd, czd of plane k - 1);
+            // then plane k + 2 goes into the p_new slot plane k - 1 left
             {
                 const P* pc = pn_ring + ps0 * PLANE_P;
                 const P* pn = pn_ring + ps1 * PLANE_P;
@@ -595,9 +631,10 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
                     czd[t] = cv.z;
                 }
             }
-            ok = k + 2 > z1 || convert(k + 2, u2, ps2);
+            const unsigned s2 = seq0 + (unsigned)(k + 2 - z0 + 1);
+            ok = k + 2 > z1 || convert(k + 2, s2, ps2);
             failed = __syncthreads_or(!ok);  // also: plane k's slot is free for plane k + 3
-            if (!failed && k + 2 <= z1) refill(k + 2);
+            if (!failed && k + 2 <= z1) refill(s2);
             const int pt = ps0;
             ps0 = ps1;
             ps1 = ps2;
@@ -622,6 +659,8 @@ __global__ void __launch_bounds__(32 * R, R == 8 ? 2 : 1) k_dpq_tma(const __grid
             acc[c0 + t].y += sm.y;
         }
         __syncthreads();
+        seq0 = seq_end;
+        npref = (int)npf;
     }
 
     if (failed) {
