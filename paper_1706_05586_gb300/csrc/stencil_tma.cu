@@ -735,6 +735,27 @@ static cudaError_t tma_configure(size_t smem, int* per_sm) {
     return e;
 }
 
+// z-chunk length of the TMA stencils' work items (a tile marched through zc planes plus
+// the two halo planes it converts).  The CTAs resident on an SM share its issue slots,
+// so the time follows the planes each SM processes: item i runs on SM i mod num_sms
+// (grids are whole multiples of the SM count), ceil(items / num_sms) items of zc + 2
+// planes.  At 1M cells x 64 complex64 columns this takes whole 64-plane columns
+// (7 x 66 planes per SM) over 32-plane chunks (14 x 34), measured 0.6% faster.
+static int zchunk_length(int tiles, int nz, int num_sms) {
+    int best = nz;
+    double best_cost = 1e300;
+    for (int zc : {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, nz}) {
+        if (zc > nz || zc < 1) continue;
+        const long items = (long)tiles * ((nz + zc - 1) / zc);
+        const double cost = (double)((items + num_sms - 1) / num_sms) * (zc + 2);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = zc;
+        }
+    }
+    return best;
+}
+
 cudaError_t tma_stencil_prepare(ElemKind inner, const DirRing& ring, const void* cf, int nx, int ny, int nz, int kp,
                                 int num_sms, TmaStencil* out) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
@@ -777,22 +798,9 @@ cudaError_t tma_stencil_prepare(ElemKind inner, const DirRing& ring, const void*
         e = kc == 32 ? tma_configure<float, 32>(out->smem, &per_sm) : tma_configure<float, 16>(out->smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    // z-chunk length: balance whole waves of items against the two halo planes per chunk
     const int tiles = (nx / TX) * (ny / TY) * (kp / kc);
     const int grid_cap = per_sm * num_sms;
-    int best = nz;
-    double best_cost = 1e300;
-    for (int zc : {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, nz}) {
-        if (zc > nz || zc < 1) continue;
-        const long items = (long)tiles * ((nz + zc - 1) / zc);
-        const long grid = items < grid_cap ? items : grid_cap;
-        const double waves = (double)((items + grid - 1) / grid);
-        const double cost = waves * (zc + 2);
-        if (cost < best_cost - 1e-9) {
-            best_cost = cost;
-            best = zc;
-        }
-    }
+    const int best = zchunk_length(tiles, nz, num_sms);
     out->zc = best;
     const long items = (long)tiles * ((nz + best - 1) / best);
     out->grid = (int)(items < grid_cap ? items : grid_cap);
@@ -901,21 +909,9 @@ cudaError_t dpq_prepare(ElemKind inner, const DirRing& ring, const void* r, cons
     cudaError_t e = cx ? dpq_configure<float2, 16>(out->smemf, &per_sm) : dpq_configure<float, 32>(out->smemf, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    // z-chunk length: whole waves of items against the two halo planes each chunk converts
     const int tiles = (nx / TX) * (ny / kDpqRows) * (kp / kc);
     const int grid_cap = per_sm * num_sms;
-    int best = nz;
-    double best_cost = 1e300;
-    for (int zc : {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, nz}) {
-        if (zc > nz || zc < 1) continue;
-        const long items = (long)tiles * ((nz + zc - 1) / zc);
-        const long grid = items < grid_cap ? items : grid_cap;
-        const double cost = (double)((items + grid - 1) / grid) * (zc + 2);
-        if (cost < best_cost - 1e-9) {
-            best_cost = cost;
-            best = zc;
-        }
-    }
+    const int best = zchunk_length(tiles, nz, num_sms);
     out->zcf = best;
     const long items = (long)tiles * ((nz + best - 1) / best);
     out->gridf = (int)(items < grid_cap ? items : grid_cap);
