@@ -55,6 +55,9 @@ def parse():
                          "of every physical source before the timed steps; for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-autograd128", action="store_true",
+                    help="skip the autograd sub-object (misfit forward + backward through the "
+                         "torch.autograd.Function at 128^3 cells, 8 optimized + 24 random columns)")
     ap.add_argument("--no-batch8", action="store_true",
                     help="skip the short eight-inversion batch measurement the default line carries")
     ap.add_argument("--stencil-path", type=int, choices=(0, 1, 2), default=None,
@@ -229,7 +232,9 @@ def p_sequence(inp, count, seed=7):
     return [inp.p0 + 1e-3 * (k + 1) * d for k in range(count)]
 
 
-def run_ours(args):
+def run_ours(args, nested=False):
+    """One measurement of the library's path; prints the JSON line (rank 0) unless nested,
+    and returns it."""
     import torch
 
     from paper_1706_05586_gb300 import dot as D
@@ -455,11 +460,29 @@ def run_ours(args):
                                             "gpu_launches", "roofline")}
         out["batch8"]["config"] = {k: b8["config"][k] for k in ("grids", "omega_over_nu", "ls", "ld", "rtol", "iters",
                                                                 "tuned", "tuned_columns", "stencil_path")}
-    if ws > 1:
+    # the differentiation workload, briefly: forward and backward of the autograd misfit at
+    # 128^3 cells with 5,000 PaLS parameters, 8 optimized (Algorithm 1 at p0, computed once
+    # before the timed steps) + 24 random simultaneous sources and detectors
+    if ws == 1 and not nested and not args.no_autograd128 and args.api == "abi" and \
+            args.workload == "dot128x128x64_w100MHz":
+        import copy
+        a = copy.copy(args)
+        a.workload, a.api, a.optimized, a.steps, a.warmup = "dot128x128x128", "autograd", 8, 3, 2
+        a.no_fp64_compare = a.no_e2e = a.no_cpu_baseline = a.no_batch8 = a.no_autograd128 = True
+        a.random_data, a.stencil_path, a.precision = False, None, "mixed"
+        ag = run_ours(a, nested=True)
+        out["autograd128"] = {k: ag[k] for k in ("value", "unit", "steps", "warmup", "ms_per_step", "clocks",
+                                                 "gpu_launches", "roofline")}
+        out["autograd128"]["metric"] = "misfit forward+backward/s (torch.autograd.Function) at 2.1M voxels"
+        out["autograd128"]["config"] = {k: ag["config"][k] for k in (
+            "workload", "grid", "n_voxels", "ns", "nd", "ls", "ld", "optimized_columns_per_side", "m0", "n_params",
+            "precision", "rtol", "krylov_iters_per_step", "relres_max", "api")}
+    if ws > 1 and not nested:
         import torch.distributed as dist
         dist.destroy_process_group()
-    if rank == 0:
+    if rank == 0 and not nested:
         print(json.dumps(out), flush=True)
+    return out
 
 
 # --------------------------------------------------------- oracle timing
