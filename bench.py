@@ -55,6 +55,9 @@ def parse():
                          "of every physical source before the timed steps; for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-c2", action="store_true",
+                    help="skip the c2 sub-object (64x64x32, plain FP64: the full evaluation over every "
+                         "physical source and detector against the sampled ones)")
     ap.add_argument("--no-autograd128", action="store_true",
                     help="skip the autograd sub-object (misfit forward + backward through the "
                          "torch.autograd.Function at 128^3 cells, 8 optimized + 24 random columns)")
@@ -223,6 +226,56 @@ def setup_problem(D, ctx, wl, inp, prec, rtol, log, random_data=False, optimized
     D.dot_set_sampling(ctx, W, V)
     D.dot_set_solver(ctx, D.PREC_MIXED if prec == "mixed" else D.PREC_FP64, rtol, 0)
     return Dfield, M, W, V
+
+
+def c2_measure(log, reps=3):
+    """The 64x64x32 plain-FP64 workload (131,072 cells, 64 x 64 physical sources and
+    detectors, 125 RBFs): the full evaluation of the misfit and its gradient (W = I,
+    V = I: every physical source and detector, 64 + 64 columns) against the sampled ones
+    of Sec. 3 (4 optimized columns from Algorithm 1 at p0 + 8 complementary random ones
+    per side, and 12 random ones per side): time per evaluation and the error of f and g
+    against the full values, at p0."""
+    import torch
+
+    from paper_1706_05586_gb300 import dot as D
+    wl = synth.WORKLOADS["dot64x64x32"]
+    inp = synth.draw(wl)
+    ctx = D.dot_create(0)
+    pals = (synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
+    try:
+        _, _, Wopt, Vopt = setup_problem(D, ctx, wl, inp, "fp64", 1e-10, log, optimized=4)
+
+        def ev(W, V):
+            D.dot_set_sampling(ctx, W, V)
+            D.dot_set_pals(ctx, inp.p0, *pals)
+            D.dot_gradient(ctx, wl.np_)                    # allocation and graph capture
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                D.dot_set_pals(ctx, inp.p0, *pals)        # every evaluation solves again
+                f, g, _ = D.dot_gradient(ctx, wl.np_)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) / reps * 1e3
+            st = D.dot_get_stats(ctx)
+            return f, g, ms, st["iters_max"], st["k"]
+
+        f0, g0, ms0, it0, k0 = ev(np.eye(wl.ns), np.eye(wl.nd))
+        out = {"workload": "dot64x64x32", "precision": "fp64", "rtol": 1e-10, "at": "p0",
+               "timing": "host clock around device-synchronised evaluations, mean of %d" % reps,
+               "full": {"columns": wl.ns + wl.nd, "block_width": k0, "ms_per_eval": round(ms0, 2), "iters": it0,
+                        "f": f0}}
+        for name, (W, V) in (("optimized_4_random_8", (Wopt, Vopt)), ("random_12", (inp.W, inp.V))):
+            f, g, ms, it, k = ev(W, V)
+            out[name] = {"columns": W.shape[1] + V.shape[1], "block_width": k, "ms_per_eval": round(ms, 2),
+                         "iters": it, "speedup_vs_full": round(ms0 / ms, 2), "f": f,
+                         "f_rel_err": abs(f - f0) / abs(f0),
+                         "g_rel_err": float(np.linalg.norm(g - g0) / np.linalg.norm(g0)),
+                         "g_cos": float(g @ g0 / (np.linalg.norm(g) * np.linalg.norm(g0)))}
+        log("c2: full %.1f ms, optimized+random %.1f ms, random %.1f ms"
+            % (ms0, out["optimized_4_random_8"]["ms_per_eval"], out["random_12"]["ms_per_eval"]))
+        return out
+    finally:
+        D.dot_destroy(ctx)
 
 
 def p_sequence(inp, count, seed=7):
@@ -460,6 +513,9 @@ def run_ours(args, nested=False):
                                             "gpu_launches", "roofline")}
         out["batch8"]["config"] = {k: b8["config"][k] for k in ("grids", "omega_over_nu", "ls", "ld", "rtol", "iters",
                                                                 "tuned", "tuned_columns", "stencil_path")}
+    # the full against the sampled evaluation on the 64x64x32 plain-FP64 workload
+    if ws == 1 and not nested and not args.no_c2 and args.api == "abi" and args.workload == "dot128x128x64_w100MHz":
+        out["c2"] = c2_measure(log)
     # the differentiation workload, briefly: forward and backward of the autograd misfit at
     # 128^3 cells with 5,000 PaLS parameters, 8 optimized (Algorithm 1 at p0, computed once
     # before the timed steps) + 24 random simultaneous sources and detectors
@@ -468,7 +524,7 @@ def run_ours(args, nested=False):
         import copy
         a = copy.copy(args)
         a.workload, a.api, a.optimized, a.steps, a.warmup = "dot128x128x128", "autograd", 8, 3, 2
-        a.no_fp64_compare = a.no_e2e = a.no_cpu_baseline = a.no_batch8 = a.no_autograd128 = True
+        a.no_fp64_compare = a.no_e2e = a.no_cpu_baseline = a.no_batch8 = a.no_autograd128 = a.no_c2 = True
         a.random_data, a.stencil_path, a.precision = False, None, "mixed"
         ag = run_ours(a, nested=True)
         out["autograd128"] = {k: ag[k] for k in ("value", "unit", "steps", "warmup", "ms_per_step", "clocks",
