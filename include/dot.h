@@ -236,10 +236,15 @@ int dot_set_launch_options(dot_ctx* ctx, int graphs, int autotune);
  * more bytes per iteration.  Errors: DOT_EINVAL for other values. */
 int dot_set_direction_ring(dot_ctx* ctx, int slots);
 /* Misfit and gradient of several contexts (independent inversions, e.g. uneven grids
- * and mixed omega) at once: their block solves advance in interleaved batches on
- * their own streams, so one context's host poll overlaps the others' kernels.  Same
- * per-context semantics and outputs as dot_gradient (f[i], g[i]); each context must
- * appear once. */
+ * and mixed omega) in one call.  The members run one after another, each on its own
+ * stream with its own launch configuration (autotuned per member when enabled) and
+ * graph-replayed block solve; each member's kernels fill the GPU by themselves, so
+ * members are not overlapped.  Same per-context semantics and outputs as dot_gradient
+ * (f[i], g[i]); each context must appear once.  The contexts, their data and the
+ * output pointers are checked before the first member runs; a member missing another
+ * input fails when its turn comes.  Returns the first hard error (later members do
+ * not run), else DOT_ENOTCONV / DOT_EBREAKDOWN if a member ended so (every member's
+ * outputs are written). */
 int dot_gradient_batch(dot_ctx* const* ctxs, int count, double* f, double* const* g);
 /* Stencil implementation of the block solve (no counterpart in the paper, which leaves
  * the solver open).  mode 2 (default): wherever the block allows it (FP32/complex64
