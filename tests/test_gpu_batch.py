@@ -73,6 +73,49 @@ def test_autotuned_launches_agree(problems):
         assert st["tuned_blocks_per_sm"] in (4, 5, 8, 16) and st["tuned_tma"] in (0, 1)
 
 
+def _tuning_direction_ms(mode):
+    """Mean CUDA-event time per launch of the separate direction passes during one
+    autotuning solve in stencil mode `mode` (64 x 64 x 32 cells, 16 + 16 complex64
+    columns, eligible for the fused kernel)."""
+    wl = synth.small_workload(64, 64, 32, 0.125, omega_nu=0.4, src_grid=(4, 4), det_grid=(4, 4), ls=16, ld=16,
+                              m0=8, sampling="gaussian", seed_index=93)
+    inp = synth.draw(wl)
+    h = D.dot_create(0)
+    try:
+        D.dot_set_grid(h, wl.nx, wl.ny, wl.nz, wl.h, wl.bc)
+        D.dot_set_omega(h, wl.omega_nu)
+        D.dot_set_diffusion(h, np.full(wl.n, 1.0 / 30.0))
+        D.dot_set_pals(h, inp.p0, synth.MU_IN, synth.MU_OUT, wl.cutoff, wl.eps, wl.gamma)
+        D.dot_set_sources(h, inp.B)
+        D.dot_set_detectors(h, inp.C)
+        D.dot_set_data(h, np.zeros((wl.nd, wl.ns)))
+        D.dot_set_sampling(h, inp.W, inp.V)
+        D.dot_set_solver(h, D.PREC_MIXED, 1e-10, 0)
+        D.dot_set_stencil_path(h, mode)
+        D.dot_set_launch_options(h, True, True)
+        D.dot_set_kernel_timing(h, 1)
+        _, _, rc = D.dot_gradient(h, wl.np_)             # the tuning solve
+        assert rc == D.DOT_OK
+        d = D.dot_get_kernel_timing(h)["direction"]
+    finally:
+        D.dot_destroy(h)
+    assert d["launches"] > 0
+    return d["ms"] / d["launches"]
+
+
+def test_autotune_candidates_run_their_configuration():
+    """Each autotuner candidate runs exactly its stencil configuration.  In stencil
+    mode 2 the fused kernel's maps are prepared, yet the candidates with a separate
+    direction pass (direct and TMA stencils) must run that pass: their direction
+    intervals then take as long per launch as in mode 1, where the same two kinds of
+    candidate are timed and no fused kernel exists.  A candidate that fused the
+    direction into the stencil while timed as a separate pass would add empty
+    intervals to mode 2's mean."""
+    m1 = _tuning_direction_ms(1)
+    m2 = _tuning_direction_ms(2)
+    assert m2 >= 0.8 * m1, (m2, m1)
+
+
 def test_batch_rejects_duplicates(problems):
     h = D.dot_create(0)
     try:
