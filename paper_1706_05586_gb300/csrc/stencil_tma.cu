@@ -325,11 +325,12 @@ __global__ void __launch_bounds__(THREADS, KC == 16 ? 3 : 2) k_pq_tma(const __gr
 // cp.async.bulk.tensor loads on one mbarrier: r~ and p_old into one of S staging slots
 // and the 32-byte records (coefficients, FP32 Jacobi inverse) into a ring of S + 3
 // coefficient planes.  The plane is then converted once, halo included, into a ring
-// of three p_new planes (k-1, k, k+1) that the stencil reads; out-of-grid cells arrive
-// as zeros in r~, p_old and M^{-1}, so their p_new is an exact zero as well.  The
-// staging slot is refilled as soon as its plane is converted, so S planes are in
-// flight while a plane is computed.  A lane owns one column (KC = 16 complex or 32
-// real columns: 128-byte rows).
+// of three p_new planes (k, k + 1 and the one being converted; the -z neighbours of
+// plane k stay in registers) that the stencil reads; out-of-grid cells arrive as zeros
+// in r~, p_old and M^{-1}, so their p_new is an exact zero as well.  A staging slot is
+// refilled after the barrier that follows its plane's conversion, so S planes are in
+// flight while a plane is computed.  A lane carries 16 bytes of columns (two complex
+// or four real) of one cell; KC = 16 complex or 32 real columns make 128-byte rows.
 template <typename T, int KC, int S, int R>
 struct DpqLayout {
     static constexpr int HYR = R + 2;                          // halo rows of an R-row tile
